@@ -1,0 +1,142 @@
+"""DialSort CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, single-threaded definitions of what the DialSort hot path
+computes, written in C (``dialsort_oracle.c``) from the paper's equations and
+wrapped here with ctypes.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the CUDA product path
+never does, and the two share no code.
+
+Functions and the passages they follow:
+
+* ``histogram``   -- Eq. (1), ingestion, with H zeroed first (Theorem
+  "Sequential complexity": the Theta(U) initialisation).
+* ``reconstruct`` -- Eq. (2), ordered projection.
+* ``sort``        -- Eq. (1) then Eq. (2) (Theorem "Correctness of DialSort").
+* ``offsets``     -- the cursor of the sequential projection of Eq. (2) on
+  reaching each k: O[k] = sum_{j<k} H[j].
+* ``crn_level`` / ``crn`` -- Definition "CRN level transition" with the node
+  rule of Eqs. (3)-(4).
+
+Every function is pinned by ``tests/test_oracle_pins.py`` against the paper's
+worked examples, brute force, library routines and the theorems' invariants.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dialsort_oracle.c")
+_LIB = os.path.join(_HERE, "libdialsort_oracle.so")
+_lib = None
+
+_P = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+_U32 = ctypes.c_uint32
+_SZ = ctypes.c_size_t
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (single-threaded, no vectorisation flags)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
+    os.close(fd)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC], check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        for name in ("oracle_histogram_u32", "oracle_histogram_u16"):
+            f = getattr(lib, name)
+            f.restype = _U64
+            f.argtypes = [_P, _U64, _U32, _P]
+        for name in ("oracle_reconstruct_u32", "oracle_reconstruct_u16"):
+            f = getattr(lib, name)
+            f.restype = _U64
+            f.argtypes = [_P, _U32, _P, _U64]
+        lib.oracle_offsets.restype = None
+        lib.oracle_offsets.argtypes = [_P, _U32, _P]
+        lib.oracle_crn_level.restype = _SZ
+        lib.oracle_crn_level.argtypes = [_P, _P, _SZ, _P, _P]
+        lib.oracle_crn.restype = _SZ
+        lib.oracle_crn.argtypes = [_P, _P, _SZ, _P, _P]
+        _lib = lib
+    return _lib
+
+
+def _c(a: np.ndarray, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def histogram(keys: np.ndarray, U: int) -> tuple[np.ndarray, int]:
+    """Eq. (1). Returns (H as uint32[U], number of keys >= U that were skipped)."""
+    keys = np.asarray(keys)
+    H = np.empty(U, dtype=np.uint32)
+    if keys.dtype == np.uint16:
+        k = _c(keys, np.uint16)
+        skipped = _load().oracle_histogram_u16(k.ctypes.data, k.size, U, H.ctypes.data)
+    else:
+        k = _c(keys, np.uint32)
+        skipped = _load().oracle_histogram_u32(k.ctypes.data, k.size, U, H.ctypes.data)
+    return H, int(skipped)
+
+
+def reconstruct(H: np.ndarray, U: int | None = None, width: int = 4, cap: int | None = None) -> np.ndarray:
+    """Eq. (2). Emits k exactly H[k] times for k = 0..U-1 (uint32 or uint16 output)."""
+    H = _c(H, np.uint32)
+    U = H.size if U is None else U
+    total = int(H[:U].astype(np.uint64).sum())
+    cap = total if cap is None else cap
+    if width == 4:
+        out = np.empty(cap, dtype=np.uint32)
+        n = _load().oracle_reconstruct_u32(H.ctypes.data, U, out.ctypes.data, cap)
+    else:
+        out = np.empty(cap, dtype=np.uint16)
+        n = _load().oracle_reconstruct_u16(H.ctypes.data, U, out.ctypes.data, cap)
+    assert n == total
+    return out
+
+
+def sort(keys: np.ndarray, U: int) -> np.ndarray:
+    """Eq. (1) followed by Eq. (2)."""
+    keys = np.asarray(keys)
+    H, _ = histogram(keys, U)
+    return reconstruct(H, U, width=2 if keys.dtype == np.uint16 else 4)
+
+
+def offsets(H: np.ndarray, U: int | None = None) -> np.ndarray:
+    """O[k] = sum_{j<k} H[j] for k = 0..U, as uint64[U+1]."""
+    H = _c(H, np.uint32)
+    U = H.size if U is None else U
+    O = np.empty(U + 1, dtype=np.uint64)
+    _load().oracle_offsets(H.ctypes.data, U, O.ctypes.data)
+    return O
+
+
+def crn_level(keys, counts) -> tuple[np.ndarray, np.ndarray]:
+    """One level of Definition "CRN level transition"."""
+    k = _c(keys, np.uint32)
+    c = _c(counts, np.uint64)
+    ko = np.empty(max(k.size, 1), dtype=np.uint32)
+    co = np.empty(max(k.size, 1), dtype=np.uint64)
+    m = _load().oracle_crn_level(k.ctypes.data, c.ctypes.data, k.size, ko.ctypes.data, co.ctypes.data)
+    return ko[:m].copy(), co[:m].copy()
+
+
+def crn(keys, counts=None) -> tuple[np.ndarray, np.ndarray]:
+    """ceil(log2 k) CRN levels over k lanes; returns the surviving (key, count) items."""
+    k = _c(keys, np.uint32).copy()
+    c = np.ones(k.size, dtype=np.uint64) if counts is None else _c(counts, np.uint64).copy()
+    sk = np.empty(max(k.size, 1), dtype=np.uint32)
+    sc = np.empty(max(k.size, 1), dtype=np.uint64)
+    m = _load().oracle_crn(k.ctypes.data, c.ctypes.data, k.size, sk.ctypes.data, sc.ctypes.data)
+    return k[:m].copy(), c[:m].copy()

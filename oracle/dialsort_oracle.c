@@ -1,0 +1,151 @@
+/*
+ * DialSort CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded restatement of what the DialSort hot path
+ * computes, written from the paper's definitions.  Only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may load it.  It shares no code,
+ * header, table or helper with the CUDA path.
+ *
+ * Paper: A. Narvaez, "DialSort: Non-Comparative Integer Sorting via the
+ * Self-Indexing Principle" (2026).
+ *
+ *   oracle_histogram_*   Eq. (1), ingestion: H initialised to zero, then
+ *                        H[x] <- H[x] + 1 for every key x of K
+ *                        (Sec. "Mathematical Formulation, Correctness, and
+ *                        Ordered Projection"; zeroing is the Theta(U) term of
+ *                        Theorem "Sequential complexity").
+ *   oracle_reconstruct_* Eq. (2), ordered projection: for k = 0..U-1 emit k
+ *                        exactly H[k] times.
+ *   oracle_offsets       where each k's run starts in the projection of
+ *                        Eq. (2): O[k] = sum_{j<k} H[j] (the cursor position
+ *                        of the sequential projection when it reaches k).
+ *   oracle_crn_level     one level of Definition "CRN level transition"
+ *                        (node rule Eqs. (3)-(4)): adjacent items paired,
+ *                        equal keys merged additively, distinct keys and an
+ *                        odd residual forwarded unchanged.
+ *   oracle_crn           ceil(log2 k) such levels applied in turn.
+ *
+ * Keys outside [0, U) are not defined by the paper; the oracle does not count
+ * them and returns how many it skipped.
+ */
+#include <stdint.h>
+#include <stddef.h>
+
+/* Eq. (1): zero H, then one increment per key. Returns the number of keys >= U. */
+uint64_t oracle_histogram_u32(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H) {
+  for (uint64_t k = 0; k < U; ++k) H[k] = 0;
+  uint64_t skipped = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    uint32_t x = keys[i];
+    if (x < U)
+      H[x] = H[x] + 1;
+    else
+      skipped = skipped + 1;
+  }
+  return skipped;
+}
+
+uint64_t oracle_histogram_u16(const uint16_t* keys, uint64_t n, uint32_t U, uint32_t* H) {
+  for (uint64_t k = 0; k < U; ++k) H[k] = 0;
+  uint64_t skipped = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    uint32_t x = keys[i];
+    if (x < U)
+      H[x] = H[x] + 1;
+    else
+      skipped = skipped + 1;
+  }
+  return skipped;
+}
+
+/*
+ * Eq. (2): for k = 0, 1, ..., U-1 emit k exactly H[k] times.  Writes at most
+ * `cap` keys into out and returns the total number emitted (sum of H), so a
+ * caller can tell when out was too small.
+ */
+uint64_t oracle_reconstruct_u32(const uint32_t* H, uint32_t U, uint32_t* out, uint64_t cap) {
+  uint64_t pos = 0;
+  for (uint64_t k = 0; k < U; ++k) {
+    for (uint64_t j = 0; j < H[k]; ++j) {
+      if (pos < cap) out[pos] = (uint32_t)k;
+      pos = pos + 1;
+    }
+  }
+  return pos;
+}
+
+uint64_t oracle_reconstruct_u16(const uint32_t* H, uint32_t U, uint16_t* out, uint64_t cap) {
+  uint64_t pos = 0;
+  for (uint64_t k = 0; k < U; ++k) {
+    for (uint64_t j = 0; j < H[k]; ++j) {
+      if (pos < cap) out[pos] = (uint16_t)k;
+      pos = pos + 1;
+    }
+  }
+  return pos;
+}
+
+/* The cursor of the sequential projection on reaching k: O[k] = sum_{j<k} H[j], O[U] = sum H. */
+void oracle_offsets(const uint32_t* H, uint32_t U, uint64_t* O) {
+  uint64_t cursor = 0;
+  for (uint64_t k = 0; k < U; ++k) {
+    O[k] = cursor;
+    cursor = cursor + H[k];
+  }
+  O[U] = cursor;
+}
+
+/*
+ * One CRN level (Definition "CRN level transition"): the m items
+ * (key_in[i], cnt_in[i]) are grouped into consecutive pairs (0,1), (2,3), ...
+ * A pair with equal keys becomes one item (key, c1 + c2) (Eq. (3)); a pair
+ * with distinct keys is forwarded unchanged (Eq. (4)); when m is odd the last
+ * item is forwarded unchanged.  Returns the number of items written to the
+ * output arrays (at most m).  Only equality between keys is evaluated.
+ */
+size_t oracle_crn_level(const uint32_t* key_in, const uint64_t* cnt_in, size_t m, uint32_t* key_out,
+                        uint64_t* cnt_out) {
+  size_t w = 0;
+  size_t i = 0;
+  for (; i + 1 < m; i += 2) {
+    if (key_in[i] == key_in[i + 1]) {
+      key_out[w] = key_in[i];
+      cnt_out[w] = cnt_in[i] + cnt_in[i + 1];
+      w = w + 1;
+    } else {
+      key_out[w] = key_in[i];
+      cnt_out[w] = cnt_in[i];
+      w = w + 1;
+      key_out[w] = key_in[i + 1];
+      cnt_out[w] = cnt_in[i + 1];
+      w = w + 1;
+    }
+  }
+  if (i < m) { /* odd residual */
+    key_out[w] = key_in[i];
+    cnt_out[w] = cnt_in[i];
+    w = w + 1;
+  }
+  return w;
+}
+
+/*
+ * The whole network for k = m lanes: L = ceil(log2 m) levels applied in turn.
+ * key/cnt hold the lane states on entry and the surviving items on return;
+ * scratch_key/scratch_cnt must hold m entries.  Returns the number of
+ * surviving items.
+ */
+size_t oracle_crn(uint32_t* key, uint64_t* cnt, size_t m, uint32_t* scratch_key, uint64_t* scratch_cnt) {
+  size_t levels = 0;
+  while (((size_t)1 << levels) < m) levels = levels + 1;
+  size_t cur = m;
+  for (size_t l = 0; l < levels; ++l) {
+    size_t next = oracle_crn_level(key, cnt, cur, scratch_key, scratch_cnt);
+    for (size_t i = 0; i < next; ++i) {
+      key[i] = scratch_key[i];
+      cnt[i] = scratch_cnt[i];
+    }
+    cur = next;
+  }
+  return cur;
+}

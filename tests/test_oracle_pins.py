@@ -1,0 +1,230 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+None of these checks retypes the oracle's own loop: each compares it with a
+value the paper prints (tests/golden), brute force over every tiny input, a
+library routine (sorted, numpy sort/cumsum/bincount), or an invariant of
+Theorem "Correctness of DialSort" / Lemma "CRN additive conservation".
+"""
+import collections
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from conftest import load_golden
+
+
+# ---------------------------------------------------------------- worked examples
+
+def test_fig_viz_worked_example():
+    g = load_golden("fig_viz.txt")
+    U = g["U"][0]
+    H, skipped = oracle.histogram(np.array(g["keys"], dtype=np.uint32), U)
+    assert skipped == 0
+    assert H.tolist() == g["H"]
+    assert oracle.reconstruct(H, U).tolist() == g["out"]
+    assert oracle.sort(np.array(g["keys"], dtype=np.uint32), U).tolist() == g["out"]
+
+
+@pytest.mark.parametrize("name", ["abacus.txt", "physical.txt"])
+def test_projection_worked_examples(name):
+    g = load_golden(name)
+    U = g["U"][0]
+    H = np.array(g["H"], dtype=np.uint32)
+    out = oracle.reconstruct(H, U)
+    assert out.tolist() == g["out"]
+    # ingesting the projected output gives the printed state back
+    H2, _ = oracle.histogram(out, U)
+    assert H2.tolist() == g["H"]
+
+
+def test_three_arrivals_of_42():
+    g = load_golden("crn_three_42.txt")
+    k, c = oracle.crn(g["lanes"])
+    assert k.tolist() == g["crn_out_keys"] and c.tolist() == g["crn_out_counts"]
+    H, _ = oracle.histogram(np.array(g["lanes"], dtype=np.uint32), g["U"][0])
+    assert int(H[42]) == g["H42"][0] and int(H.sum()) == 3
+
+
+# ---------------------------------------------------------------- brute force
+
+@pytest.mark.parametrize("U", [1, 2, 3, 4])
+def test_brute_force_all_tiny_inputs(U):
+    """Every key sequence of length 0..6 over [0, U): H against list.count, output against sorted()."""
+    for n in range(0, 7):
+        for seq in itertools.product(range(U), repeat=n):
+            keys = np.array(seq, dtype=np.uint32)
+            H, skipped = oracle.histogram(keys, U)
+            assert skipped == 0
+            assert H.tolist() == [list(seq).count(k) for k in range(U)]
+            assert oracle.reconstruct(H, U).tolist() == sorted(seq)
+
+
+def test_brute_force_u16_matches_u32_widened():
+    for n in range(0, 6):
+        for seq in itertools.product(range(3), repeat=n):
+            a = np.array(seq, dtype=np.uint16)
+            H16, _ = oracle.histogram(a, 3)
+            H32, _ = oracle.histogram(a.astype(np.uint32), 3)
+            assert H16.tolist() == H32.tolist()
+            assert oracle.reconstruct(H16, 3, width=2).tolist() == sorted(seq)
+
+
+# ---------------------------------------------------------------- library routines and invariants
+
+DISTS = ["uniform", "zipf", "all_equal", "sorted", "reverse", "runs", "paper_skew", "zipf_perm"]
+
+
+@pytest.mark.parametrize("dist", DISTS)
+@pytest.mark.parametrize("n,U", [(1000, 1), (4099, 7), (1 << 16, 256), (100_003, 1 << 12), (1 << 20, 1 << 16)])
+def test_sort_equals_numpy_sort(dist, n, U):
+    keys = gen.keys(n, U, dist, param=4096 if dist == "runs" else None, stream=11)
+    out = oracle.sort(keys, U)
+    assert out.dtype == np.uint32 and out.size == n  # Theorem "Correctness": length n
+    np.testing.assert_array_equal(out, np.sort(keys, kind="stable"))
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "all_equal", "paper_skew"])
+def test_correctness_theorem_invariants(dist):
+    n, U = 200_001, 5000
+    keys = gen.keys(n, U, dist, stream=12)
+    H, _ = oracle.histogram(keys, U)
+    assert int(H.astype(np.uint64).sum()) == n  # sum H = n
+    np.testing.assert_array_equal(H, np.bincount(keys, minlength=U).astype(np.uint32))
+    out = oracle.reconstruct(H, U)
+    assert out.size == n
+    assert np.all(out[1:] >= out[:-1])  # nondecreasing
+    assert collections.Counter(out.tolist()) == collections.Counter(keys.tolist())  # same multiset
+
+
+def test_u16_equals_u32_on_widened_keys():
+    keys16 = gen.keys(300_007, 1 << 16, "zipf", width=2, stream=13)
+    H16, _ = oracle.histogram(keys16, 1 << 16)
+    H32, _ = oracle.histogram(keys16.astype(np.uint32), 1 << 16)
+    np.testing.assert_array_equal(H16, H32)
+    out16 = oracle.reconstruct(H16, 1 << 16, width=2)
+    assert out16.dtype == np.uint16
+    np.testing.assert_array_equal(out16, np.sort(keys16))
+
+
+# ---------------------------------------------------------------- special cases
+
+def test_all_equal_is_a_fill():
+    keys = np.full(12345, 77, dtype=np.uint32)
+    H, _ = oracle.histogram(keys, 100)
+    assert int(H[77]) == 12345 and int(H.sum()) == 12345
+    assert np.all(oracle.reconstruct(H, 100) == 77)
+
+
+def test_universe_of_one():
+    keys = np.zeros(999, dtype=np.uint32)
+    H, _ = oracle.histogram(keys, 1)
+    assert H.tolist() == [999]
+    assert np.all(oracle.reconstruct(H, 1) == 0)
+
+
+def test_sorted_input_is_a_fixed_point():
+    keys = gen.keys(50_000, 1 << 10, "sorted", stream=14)
+    assert np.all(keys[1:] >= keys[:-1])
+    np.testing.assert_array_equal(oracle.sort(keys, 1 << 10), keys)
+
+
+def test_empty_input_and_empty_histogram():
+    H, skipped = oracle.histogram(np.zeros(0, dtype=np.uint32), 17)
+    assert skipped == 0 and H.tolist() == [0] * 17
+    assert oracle.reconstruct(H, 17).size == 0
+
+
+def test_out_of_range_keys_are_skipped():
+    keys = np.array([0, 5, 9, 10, 11, 4_000_000_000, 9], dtype=np.uint32)
+    H, skipped = oracle.histogram(keys, 10)
+    assert skipped == 3
+    np.testing.assert_array_equal(H, np.bincount(keys[keys < 10], minlength=10).astype(np.uint32))
+
+
+def test_reconstruct_cap_truncates_but_reports_total():
+    H = np.array([2, 0, 3], dtype=np.uint32)
+    out = oracle.reconstruct(H, 3, cap=4)
+    assert out.tolist() == [0, 0, 2, 2]
+
+
+# ---------------------------------------------------------------- offsets
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "all_equal"])
+def test_offsets_against_cumsum_and_first_occurrence(dist):
+    U = 3000
+    keys = gen.keys(77_777, U, dist, stream=15)
+    H, _ = oracle.histogram(keys, U)
+    O = oracle.offsets(H)
+    assert O.size == U + 1 and int(O[0]) == 0 and int(O[U]) == keys.size
+    np.testing.assert_array_equal(O[1:], np.cumsum(H.astype(np.uint64)))
+    out = oracle.reconstruct(H, U)
+    present = np.nonzero(H)[0]
+    # the run of each present key starts exactly at its offset
+    np.testing.assert_array_equal(np.searchsorted(out, present, side="left"), O[present])
+
+
+# ---------------------------------------------------------------- CRN (Definition "CRN level transition")
+
+def _totals(keys, counts):
+    t = collections.Counter()
+    for k, c in zip(np.asarray(keys).tolist(), np.asarray(counts).tolist()):
+        t[k] += c
+    return t
+
+
+def test_crn_level_pairs_adjacent_items_only():
+    k, c = oracle.crn_level([7, 7, 9, 9], [1, 1, 1, 1])
+    assert k.tolist() == [7, 9] and c.tolist() == [2, 2]
+    k, c = oracle.crn_level([7, 9, 9, 7], [1, 1, 1, 1])  # (7,9) and (9,7): nothing merges
+    assert k.tolist() == [7, 9, 9, 7] and c.tolist() == [1, 1, 1, 1]
+    k, c = oracle.crn_level([5, 5, 5], [2, 3, 4])  # odd residual forwarded unchanged
+    assert k.tolist() == [5, 5] and c.tolist() == [5, 4]
+    k, c = oracle.crn_level([], [])
+    assert k.size == 0
+
+
+@pytest.mark.parametrize("m", list(range(1, 33)))
+def test_crn_all_equal_lanes_collapse_in_ceil_log2_levels(m):
+    k, c = oracle.crn([3] * m)
+    assert k.tolist() == [3] and c.tolist() == [m]
+    if m > 2:
+        # one level fewer than ceil(log2 m) leaves more than one item
+        levels = math.ceil(math.log2(m))
+        kk, cc = np.array([3] * m, dtype=np.uint32), np.ones(m, dtype=np.uint64)
+        for _ in range(levels - 1):
+            kk, cc = oracle.crn_level(kk, cc)
+        assert kk.size > 1
+
+
+def test_crn_alternating_keys_never_merge():
+    """(a,b,a,b): no adjacent pair is ever equal, so the literal network forwards all four items.
+
+    The definition's closing sentence says every key survives at most once;
+    this input shows the pairing rule alone does not give that, so only the
+    additive conservation of the lemma is asserted elsewhere.
+    """
+    k, c = oracle.crn([1, 2, 1, 2])
+    assert k.tolist() == [1, 2, 1, 2] and c.tolist() == [1, 1, 1, 1]
+
+
+@pytest.mark.parametrize("m", [2, 3, 5, 7, 8, 13, 16, 31, 32])
+def test_crn_additive_conservation(m):
+    rng = np.random.default_rng(1000 + m)
+    for trial in range(200):
+        keys = rng.integers(0, 1 + trial % 6, size=m).astype(np.uint32)
+        counts = rng.integers(1, 5, size=m).astype(np.uint64)
+        before = _totals(keys, counts)
+        kk, cc = keys, counts
+        for _ in range(math.ceil(math.log2(m))):
+            kk, cc = oracle.crn_level(kk, cc)
+            assert _totals(kk, cc) == before  # invariant at every level
+        kf, cf = oracle.crn(keys, counts)
+        assert _totals(kf, cf) == before
+        # applying the surviving items to H gives the plain histogram of the lanes
+        H = np.zeros(8, dtype=np.uint64)
+        np.add.at(H, kf.astype(np.int64), cf)
+        np.testing.assert_array_equal(H, np.bincount(keys, weights=counts, minlength=8).astype(np.uint64))
