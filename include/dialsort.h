@@ -1,0 +1,180 @@
+/*
+ * dialsort.h -- C ABI of libdialsort.so, a GB300 (sm_103a) implementation of
+ * the data-parallel hot path of DialSort (A. Narvaez, "DialSort:
+ * Non-Comparative Integer Sorting via the Self-Indexing Principle", 2026).
+ *
+ * The path has two steps:
+ *   1. Ingestion, Eq. (1): H[0..U) is zeroed and H[x] += 1 for every key x.
+ *      Concurrent equal keys are merged before they reach memory, as the
+ *      Conflict Resolution Network of Sec. "Conflict Resolution Network (CRN)"
+ *      does (node rule Eqs. (3)-(4), Definition "CRN level transition"): on the
+ *      GPU a warp groups equal keys with match.any, sums their counts with
+ *      redux.add, and one leader lane applies the sum.  Only equality between
+ *      keys is evaluated (Definition "Order comparison").
+ *   2. Ordered projection, Eq. (2): for k = 0..U-1, emit k exactly H[k] times.
+ *      Placing runs in parallel needs each run's start (the cursor of the
+ *      sequential projection); a chunk-level offset scan provides it.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named keys, H, out, ws are DEVICE pointers owned by the caller.
+ *     Descriptor arrays passed to the batched entry points are HOST pointers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are asynchronous on that stream; nothing is synchronised unless the
+ *     entry point says so.
+ *   - The library allocates no device memory on these paths: scratch lives in
+ *     the caller's workspace (`ws`, `ws_bytes`), sized by the *_workspace_size
+ *     queries.  Workspace must be 256-byte aligned and must not be shared by
+ *     calls that may run concurrently.
+ *   - Argument errors are found on the host, before any launch, and returned
+ *     synchronously.  Errors found by kernels (a key >= U, a scan that gave up
+ *     waiting, a histogram whose total exceeds the output) set bits in a
+ *     per-device error word, read and cleared by dialsort_stream_status().
+ *   - Keys must be aligned to their own width; H must be 16-byte aligned.
+ *     keys and out may be at any such alignment (unaligned heads and tails are
+ *     handled).  n < 2^32 and 1 <= U < 2^32.
+ */
+#ifndef DIALSORT_H
+#define DIALSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DIALSORT_OK = 0,
+  DIALSORT_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or width */
+  DIALSORT_ERR_KEY_RANGE = 2,   /* a kernel saw a key >= U; that key was not counted */
+  DIALSORT_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  DIALSORT_ERR_BUDGET = 4,      /* a served request cannot fit the server's HBM budget */
+  DIALSORT_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  DIALSORT_ERR_BUSY = 6,        /* a served request is not finished yet */
+  DIALSORT_ERR_OVERFLOW = 7,    /* sum(H) exceeds the output capacity n; output truncated to n */
+  DIALSORT_ERR_WORKSPACE = 8,   /* workspace too small or misaligned */
+} dialsort_status_t;
+
+/* How step 1 privatises H (the autotuner picks one when AUTO is given). */
+typedef enum {
+  DIALSORT_REGIME_AUTO = 0,
+  DIALSORT_REGIME_SMEM32 = 1,     /* per-CTA 32-bit sub-histograms in shared memory, merged into H */
+  DIALSORT_REGIME_SMEM16 = 2,     /* per-CTA packed 16-bit sub-histograms with exact carry spill */
+  DIALSORT_REGIME_CLUSTER = 3,    /* one packed sub-histogram spread over a CTA cluster's shared memory */
+  DIALSORT_REGIME_GLOBAL_CRN = 4, /* warp CRN, then one L2 atomic per distinct key of the warp */
+  DIALSORT_REGIME_GLOBAL = 5,     /* one L2 atomic per key run of a thread (no cross-lane merge) */
+} dialsort_regime_t;
+
+/* Launch choices for step 1.  Zero in any field means "pick automatically". */
+typedef struct {
+  uint32_t regime;   /* dialsort_regime_t */
+  uint32_t crn;      /* 0 = auto, 1 = warp CRN on, 2 = off (the per-thread run merge always runs) */
+  uint32_t blocks;   /* grid size */
+  uint32_t threads;  /* CTA size: 256, 512 or 1024 */
+  uint32_t replicas; /* shared-memory sub-histogram copies per CTA (SMEM32 / SMEM16) */
+  uint32_t cluster;  /* CTAs per cluster (CLUSTER regime): 2, 4, 8 or 16 */
+} dialsort_hist_config_t;
+
+/* ---------------------------------------------------------------- step 1: ingestion, Eq. (1) */
+
+/*
+ * H[0..U) := multiplicity of each k among keys[0..n) (uint32 keys).  H is
+ * overwritten (zeroed, then counted).  Keys >= U are skipped and raise
+ * DIALSORT_ERR_KEY_RANGE in the error word.  n may be 0 (H is zeroed).
+ */
+dialsort_status_t dialsort_histogram(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* stream);
+
+/* As dialsort_histogram for uint16 keys; requires U <= 65536. */
+dialsort_status_t dialsort_histogram_u16(const uint16_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* stream);
+
+/*
+ * As dialsort_histogram with explicit launch choices (key_bytes = 4 or 2).
+ * cfg may be NULL (= all automatic).  Invalid combinations (e.g. a shared
+ * memory regime whose sub-histogram does not fit) return INVALID_ARG.
+ */
+dialsort_status_t dialsort_histogram_ex(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
+                                        const dialsort_hist_config_t* cfg, void* stream);
+
+/*
+ * The autotuner's choice for a histogram of n keys of key_bytes over [0,U)
+ * with the given skew hint (0 = unknown, 1 = low conflict, 2 = skewed).
+ * Host only; writes *cfg with every field filled in.
+ */
+dialsort_status_t dialsort_plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
+                                          dialsort_hist_config_t* cfg);
+
+/* ---------------------------------------------------------------- step 2: ordered projection, Eq. (2) */
+
+/* Bytes of workspace dialsort_reconstruct / dialsort_offsets need for (U, n). */
+size_t dialsort_reconstruct_workspace_size(uint32_t U, uint64_t n);
+
+/*
+ * out[0..sum(H)) := k repeated H[k] times for k = 0..U-1 (Eq. (2)).  n is
+ * the capacity of out (normally the n the histogram was built from, which
+ * equals sum(H)).  If sum(H) > n only n keys are written and
+ * DIALSORT_ERR_OVERFLOW is raised in the error word; if sum(H) < n,
+ * out[sum(H)..n) is left untouched.  out may alias the keys that H was built
+ * from (the in-place projection of Sec. "DialSort vs. Classic Counting
+ * Sort"); it must not overlap H or ws.
+ */
+dialsort_status_t dialsort_reconstruct(const uint32_t* H, uint32_t U, uint32_t* out, uint64_t n, void* ws,
+                                       size_t ws_bytes, void* stream);
+
+/* As dialsort_reconstruct writing uint16 keys; requires U <= 65536. */
+dialsort_status_t dialsort_reconstruct_u16(const uint32_t* H, uint32_t U, uint16_t* out, uint64_t n, void* ws,
+                                           size_t ws_bytes, void* stream);
+
+/*
+ * The offset scan of step 2 alone (it is the first kernel of
+ * dialsort_reconstruct): writes, into ws, the start of every 1024-bin chunk's
+ * run in the output and the first chunk of every 8192-key output tile.  Exposed
+ * so the scan can be timed and checked separately.  dialsort_read_chunk_offsets
+ * copies the chunk starts (ceil(U/1024) + 1 uint64 values, the last = sum(H))
+ * to a device array.
+ */
+dialsort_status_t dialsort_offsets(const uint32_t* H, uint32_t U, uint64_t n, void* ws, size_t ws_bytes,
+                                   void* stream);
+dialsort_status_t dialsort_read_chunk_offsets(const void* ws, uint32_t U, uint64_t n, uint64_t* chunk_offsets,
+                                              void* stream);
+
+/* ---------------------------------------------------------------- both steps */
+
+/* Bytes of workspace dialsort_sort needs: H (4U bytes) plus the scan scratch. */
+size_t dialsort_sort_workspace_size(uint64_t n, uint32_t U);
+
+/*
+ * Sorts keys[0..n) into out[0..n) by Eq. (1) then Eq. (2).  H is kept at the
+ * start of ws (dialsort_sort_histogram(ws) returns it).  out may equal keys
+ * (in place).
+ */
+dialsort_status_t dialsort_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* out, void* ws,
+                                size_t ws_bytes, void* stream);
+dialsort_status_t dialsort_sort_u16(const uint16_t* keys, uint64_t n, uint32_t U, uint16_t* out, void* ws,
+                                    size_t ws_bytes, void* stream);
+/* Device pointer to the histogram that dialsort_sort leaves in ws. */
+uint32_t* dialsort_sort_histogram(void* ws);
+
+/* ---------------------------------------------------------------- status */
+
+/*
+ * Reads and clears the error word of the current device.  With sync != 0 the
+ * stream is synchronised first, so every kernel launched on it so far has
+ * reported.  The word is per device, not per stream: errors from work on
+ * other streams of the same device show up here too.
+ */
+dialsort_status_t dialsort_stream_status(void* stream, int sync);
+
+/* A short English description of a status code (static storage). */
+const char* dialsort_status_string(dialsort_status_t status);
+
+/* Number of SMs of the current device (0 if there is no usable device). */
+int dialsort_device_sm_count(void);
+
+/* Library version string, e.g. "dialsort-gb300 0.1.0 sm_103a". */
+const char* dialsort_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIALSORT_H */

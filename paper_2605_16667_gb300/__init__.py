@@ -1,0 +1,173 @@
+"""DialSort hot path on GB300 (sm_103a): tensor-level Python binding.
+
+Thin wrappers over the C ABI of ``libdialsort.so`` (``include/dialsort.h``).
+PyTorch supplies device memory and streams only; every step runs in the
+library's CUDA kernels, and a missing library or a non-CUDA tensor is an
+error (there is no CPU fallback).
+
+Keys are 32-bit (torch.int32 / torch.uint32 storage, read as uint32) or
+16-bit (torch.int16 / torch.uint16, read as uint16).  Histograms are uint32
+values held in torch.int32 tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import native
+
+__all__ = [
+    "DialSortError", "histogram", "reconstruct", "sort", "offsets", "plan_histogram", "stream_status",
+    "sort_workspace_size", "reconstruct_workspace_size", "REGIMES", "lib",
+]
+
+OK, ERR_INVALID_ARG, ERR_KEY_RANGE, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_BUSY, ERR_OVERFLOW, ERR_WORKSPACE = range(9)
+
+REGIMES = {"auto": 0, "smem32": 1, "smem16": 2, "cluster": 3, "global_crn": 4, "global": 5}
+REGIME_NAMES = {v: k for k, v in REGIMES.items()}
+
+_W4 = (torch.int32, torch.uint32)
+_W2 = (torch.int16, torch.uint16)
+
+
+class DialSortError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = native.load().dialsort_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})")
+        self.status = status
+
+
+def lib():
+    """The loaded ctypes library (raises if it is not built)."""
+    return native.load()
+
+
+def _check(status: int, what: str) -> None:
+    if status != OK:
+        raise DialSortError(status, what)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _width(t: torch.Tensor) -> int:
+    if t.dtype in _W4:
+        return 4
+    if t.dtype in _W2:
+        return 2
+    raise TypeError(f"keys must be 32- or 16-bit integers, got {t.dtype}")
+
+
+def _cuda(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (DialSort has no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _config(config) -> ctypes.c_void_p | None:
+    if config is None:
+        return None
+    c = native.dialsort_hist_config_t()
+    for k, v in config.items():
+        if k == "regime" and isinstance(v, str):
+            v = REGIMES[v]
+        if k == "crn" and isinstance(v, bool):
+            v = 1 if v else 2
+        setattr(c, k, int(v))
+    return c
+
+
+def histogram(keys: torch.Tensor, U: int, H: torch.Tensor | None = None, *, config: dict | None = None,
+              stream=None) -> torch.Tensor:
+    """Eq. (1): H[k] = number of keys equal to k, for k in [0, U).  Returns H (int32 storage of uint32)."""
+    _cuda(keys, "keys")
+    w = _width(keys)
+    if H is None:
+        H = torch.empty(U, dtype=torch.int32, device=keys.device)
+    _cuda(H, "H")
+    cfg = _config(config)
+    st = native.load().dialsort_histogram_ex(keys.data_ptr(), w, keys.numel(), U, H.data_ptr(),
+                                             ctypes.byref(cfg) if cfg is not None else None, _stream(stream))
+    _check(st, "dialsort_histogram")
+    return H
+
+
+def reconstruct_workspace_size(U: int, n: int) -> int:
+    return native.load().dialsort_reconstruct_workspace_size(U, n)
+
+
+def sort_workspace_size(n: int, U: int) -> int:
+    return native.load().dialsort_sort_workspace_size(n, U)
+
+
+def _workspace(nbytes: int, device, ws: torch.Tensor | None) -> torch.Tensor:
+    if ws is not None and ws.numel() * ws.element_size() >= nbytes:
+        return ws
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def reconstruct(H: torch.Tensor, U: int, n: int, out: torch.Tensor | None = None, *, width: int = 4,
+                ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Eq. (2): out[0..sum H) = k repeated H[k] times, k ascending.  n is out's capacity."""
+    _cuda(H, "H")
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32 if width == 4 else torch.int16, device=H.device)
+    _cuda(out, "out")
+    width = _width(out)
+    ws = _workspace(reconstruct_workspace_size(U, n), H.device, ws)
+    fn = native.load().dialsort_reconstruct if width == 4 else native.load().dialsort_reconstruct_u16
+    _check(fn(H.data_ptr(), U, out.data_ptr(), n, ws.data_ptr(), ws.numel(), _stream(stream)), "dialsort_reconstruct")
+    return out
+
+
+def offsets(H: torch.Tensor, U: int, n: int, *, ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The offset scan alone: start of every 1024-bin chunk's run (int64[ceil(U/1024)+1], last = sum H)."""
+    _cuda(H, "H")
+    ws = _workspace(reconstruct_workspace_size(U, n), H.device, ws)
+    L = native.load()
+    _check(L.dialsort_offsets(H.data_ptr(), U, n, ws.data_ptr(), ws.numel(), _stream(stream)), "dialsort_offsets")
+    chunks = (U + 1023) // 1024
+    O = torch.empty(chunks + 1, dtype=torch.int64, device=H.device)
+    _check(L.dialsort_read_chunk_offsets(ws.data_ptr(), U, n, O.data_ptr(), _stream(stream)), "read_chunk_offsets")
+    return O
+
+
+def sort(keys: torch.Tensor, U: int, out: torch.Tensor | None = None, *, ws: torch.Tensor | None = None,
+         stream=None, return_histogram: bool = False):
+    """Eq. (1) then Eq. (2).  out may be keys itself (in place)."""
+    _cuda(keys, "keys")
+    w = _width(keys)
+    n = keys.numel()
+    if out is None:
+        out = torch.empty_like(keys)
+    _cuda(out, "out")
+    if _width(out) != w:
+        raise TypeError("out must have the key width of keys")
+    nbytes = sort_workspace_size(n, U)
+    ws = _workspace(nbytes, keys.device, ws)
+    L = native.load()
+    fn = L.dialsort_sort if w == 4 else L.dialsort_sort_u16
+    _check(fn(keys.data_ptr(), n, U, out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "dialsort_sort")
+    if return_histogram:
+        return out, ws[: 4 * U].view(torch.int32)
+    return out
+
+
+def stream_status(stream=None, sync: bool = True) -> int:
+    """Read and clear the device error word (OK, ERR_KEY_RANGE, ERR_TIMEOUT, ERR_OVERFLOW)."""
+    return native.load().dialsort_stream_status(_stream(stream), 1 if sync else 0)
+
+
+def plan_histogram(n: int, U: int, width: int = 4, skew_hint: int = 0, **forced) -> dict:
+    """The autotuner's launch choices for step 1, as a dict."""
+    c = _config(forced) or native.dialsort_hist_config_t()
+    _check(native.load().dialsort_plan_histogram(n, U, width, skew_hint, ctypes.byref(c)), "plan_histogram")
+    d = {f: getattr(c, f) for f, _ in c._fields_}
+    d["regime_name"] = REGIME_NAMES[d["regime"]]
+    return d

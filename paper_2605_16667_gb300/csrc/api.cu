@@ -1,0 +1,222 @@
+// extern "C" entry points of libdialsort.so (declared in include/dialsort.h):
+// host-side argument checks, per-device state, and the launch sequences of the
+// two steps of DialSort.
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace dialsort {
+
+// The per-device error word.  Kernels receive its device address as an
+// argument; host code never dereferences the symbol.
+static __device__ uint32_t g_error_word;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+DeviceInfo g_dev[kMaxDevices];
+std::once_flag g_once[kMaxDevices];
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+dialsort_status_t from_cuda(cudaError_t e) { return e == cudaSuccess ? DIALSORT_OK : DIALSORT_ERR_CUDA; }
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+const DeviceInfo* device_info() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::call_once(g_once[dev], [dev] {
+    DeviceInfo d;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return;
+    d.sms = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return;
+    d.smem_optin = (size_t)v;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return;
+    d.err = static_cast<uint32_t*>(p);
+    d.device = dev;
+    g_dev[dev] = d;
+  });
+  return g_dev[dev].device == dev ? &g_dev[dev] : nullptr;
+}
+
+}  // namespace dialsort
+
+using namespace dialsort;
+
+namespace {
+
+dialsort_status_t check_keys(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U) {
+  if (key_bytes != 4 && key_bytes != 2) return DIALSORT_ERR_INVALID_ARG;
+  if (U == 0 || n >= (1ull << 32)) return DIALSORT_ERR_INVALID_ARG;
+  if (key_bytes == 2 && U > 65536u) return DIALSORT_ERR_INVALID_ARG;
+  if (n > 0 && (keys == nullptr || !aligned(keys, key_bytes))) return DIALSORT_ERR_INVALID_ARG;
+  return DIALSORT_OK;
+}
+
+dialsort_status_t histogram_impl(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
+                                 const dialsort_hist_config_t* cfg, cudaStream_t st) {
+  dialsort_status_t s = check_keys(keys, key_bytes, n, U);
+  if (s != DIALSORT_OK) return s;
+  if (H == nullptr || !aligned(H, 16)) return DIALSORT_ERR_INVALID_ARG;
+  const DeviceInfo* dev = device_info();
+  if (!dev) return DIALSORT_ERR_CUDA;
+  HistPlan plan;
+  s = plan_histogram(n, U, key_bytes, 0, cfg, *dev, &plan);
+  if (s != DIALSORT_OK) return s;
+  // Eq. (1) starts from H = 0: the Theta(U) initialisation
+  cudaError_t e = cudaMemsetAsync(H, 0, (size_t)U * 4, st);
+  if (e == cudaSuccess && n > 0) e = launch_histogram(keys, key_bytes, n, U, H, plan, dev->err, st);
+  return from_cuda(e);
+}
+
+dialsort_status_t reconstruct_impl(const uint32_t* H, uint32_t U, void* out, uint32_t out_bytes, uint64_t n,
+                                   void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (U == 0 || n >= (1ull << 32) || H == nullptr || !aligned(H, 16)) return DIALSORT_ERR_INVALID_ARG;
+  if (out_bytes == 2 && U > 65536u) return DIALSORT_ERR_INVALID_ARG;
+  if (n > 0 && (out == nullptr || !aligned(out, out_bytes))) return DIALSORT_ERR_INVALID_ARG;
+  const ReconLayout L = recon_layout(U, n);
+  if (ws == nullptr || !aligned(ws, 256) || ws_bytes < L.total) return DIALSORT_ERR_WORKSPACE;
+  const DeviceInfo* dev = device_info();
+  if (!dev) return DIALSORT_ERR_CUDA;
+  cudaError_t e = launch_offsets(H, U, n, ws, L, dev->err, st);
+  if (e == cudaSuccess) e = launch_expand(H, U, n, out, out_bytes, ws, L, st);
+  return from_cuda(e);
+}
+
+size_t sort_h_bytes(uint32_t U) { return align_up((size_t)U * 4, 256); }
+
+dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, void* out, void* ws,
+                            size_t ws_bytes, cudaStream_t st) {
+  dialsort_status_t s = check_keys(keys, key_bytes, n, U);
+  if (s != DIALSORT_OK) return s;
+  if (n > 0 && (out == nullptr || !aligned(out, key_bytes))) return DIALSORT_ERR_INVALID_ARG;
+  if (ws == nullptr || !aligned(ws, 256) || ws_bytes < dialsort_sort_workspace_size(n, U))
+    return DIALSORT_ERR_WORKSPACE;
+  uint32_t* H = static_cast<uint32_t*>(ws);
+  s = histogram_impl(keys, key_bytes, n, U, H, nullptr, st);
+  if (s != DIALSORT_OK) return s;
+  const size_t hb = sort_h_bytes(U);
+  return reconstruct_impl(H, U, out, key_bytes, n, static_cast<char*>(ws) + hb, ws_bytes - hb, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+dialsort_status_t dialsort_histogram(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* stream) {
+  return histogram_impl(keys, 4, n, U, H, nullptr, as_stream(stream));
+}
+
+dialsort_status_t dialsort_histogram_u16(const uint16_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* stream) {
+  return histogram_impl(keys, 2, n, U, H, nullptr, as_stream(stream));
+}
+
+dialsort_status_t dialsort_histogram_ex(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
+                                        const dialsort_hist_config_t* cfg, void* stream) {
+  return histogram_impl(keys, key_bytes, n, U, H, cfg, as_stream(stream));
+}
+
+dialsort_status_t dialsort_plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
+                                          dialsort_hist_config_t* cfg) {
+  if (cfg == nullptr || U == 0 || (key_bytes != 4 && key_bytes != 2) || skew_hint > 2)
+    return DIALSORT_ERR_INVALID_ARG;
+  DeviceInfo fallback;  // planning works without a device (152 SMs, 227 KB)
+  const DeviceInfo* dev = device_info();
+  HistPlan p;
+  dialsort_hist_config_t in = *cfg;
+  dialsort_status_t s = plan_histogram(n, U, key_bytes, skew_hint, &in, dev ? *dev : fallback, &p);
+  if (s != DIALSORT_OK) return s;
+  *cfg = dialsort_hist_config_t{p.regime, p.crn ? 1u : 2u, p.blocks, p.threads, p.replicas, p.cluster};
+  return DIALSORT_OK;
+}
+
+size_t dialsort_reconstruct_workspace_size(uint32_t U, uint64_t n) { return recon_layout(U, n).total; }
+
+dialsort_status_t dialsort_reconstruct(const uint32_t* H, uint32_t U, uint32_t* out, uint64_t n, void* ws,
+                                       size_t ws_bytes, void* stream) {
+  return reconstruct_impl(H, U, out, 4, n, ws, ws_bytes, as_stream(stream));
+}
+
+dialsort_status_t dialsort_reconstruct_u16(const uint32_t* H, uint32_t U, uint16_t* out, uint64_t n, void* ws,
+                                           size_t ws_bytes, void* stream) {
+  return reconstruct_impl(H, U, out, 2, n, ws, ws_bytes, as_stream(stream));
+}
+
+dialsort_status_t dialsort_offsets(const uint32_t* H, uint32_t U, uint64_t n, void* ws, size_t ws_bytes,
+                                   void* stream) {
+  if (U == 0 || n >= (1ull << 32) || H == nullptr || !aligned(H, 16)) return DIALSORT_ERR_INVALID_ARG;
+  const ReconLayout L = recon_layout(U, n);
+  if (ws == nullptr || !aligned(ws, 256) || ws_bytes < L.total) return DIALSORT_ERR_WORKSPACE;
+  const DeviceInfo* dev = device_info();
+  if (!dev) return DIALSORT_ERR_CUDA;
+  return from_cuda(launch_offsets(H, U, n, ws, L, dev->err, as_stream(stream)));
+}
+
+dialsort_status_t dialsort_read_chunk_offsets(const void* ws, uint32_t U, uint64_t n, uint64_t* chunk_offsets,
+                                              void* stream) {
+  if (ws == nullptr || chunk_offsets == nullptr || U == 0) return DIALSORT_ERR_INVALID_ARG;
+  const ReconLayout L = recon_layout(U, n);
+  const char* base = static_cast<const char*>(ws);
+  return from_cuda(cudaMemcpyAsync(chunk_offsets, base + L.off_offsets, 8 * (L.num_chunks + 1),
+                                   cudaMemcpyDeviceToDevice, as_stream(stream)));
+}
+
+size_t dialsort_sort_workspace_size(uint64_t n, uint32_t U) { return sort_h_bytes(U) + recon_layout(U, n).total; }
+
+dialsort_status_t dialsort_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* out, void* ws,
+                                size_t ws_bytes, void* stream) {
+  return sort_impl(keys, 4, n, U, out, ws, ws_bytes, as_stream(stream));
+}
+
+dialsort_status_t dialsort_sort_u16(const uint16_t* keys, uint64_t n, uint32_t U, uint16_t* out, void* ws,
+                                    size_t ws_bytes, void* stream) {
+  return sort_impl(keys, 2, n, U, out, ws, ws_bytes, as_stream(stream));
+}
+
+uint32_t* dialsort_sort_histogram(void* ws) { return static_cast<uint32_t*>(ws); }
+
+dialsort_status_t dialsort_stream_status(void* stream, int sync) {
+  const DeviceInfo* dev = device_info();
+  if (!dev) return DIALSORT_ERR_CUDA;
+  cudaStream_t st = as_stream(stream);
+  if (sync && cudaStreamSynchronize(st) != cudaSuccess) return DIALSORT_ERR_CUDA;
+  uint32_t word = 0;
+  // read and clear the word in stream order
+  if (cudaMemcpyAsync(&word, dev->err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return DIALSORT_ERR_CUDA;
+  if (cudaMemsetAsync(dev->err, 0, 4, st) != cudaSuccess) return DIALSORT_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return DIALSORT_ERR_CUDA;
+  if (word & ERRBIT_TIMEOUT) return DIALSORT_ERR_TIMEOUT;
+  if (word & ERRBIT_OVERFLOW) return DIALSORT_ERR_OVERFLOW;
+  if (word & ERRBIT_KEY_RANGE) return DIALSORT_ERR_KEY_RANGE;
+  return DIALSORT_OK;
+}
+
+const char* dialsort_status_string(dialsort_status_t s) {
+  switch (s) {
+    case DIALSORT_OK: return "ok";
+    case DIALSORT_ERR_INVALID_ARG: return "invalid argument";
+    case DIALSORT_ERR_KEY_RANGE: return "a key was outside [0, U) and was not counted";
+    case DIALSORT_ERR_CUDA: return "CUDA runtime error";
+    case DIALSORT_ERR_BUDGET: return "request does not fit the HBM budget";
+    case DIALSORT_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+    case DIALSORT_ERR_BUSY: return "not finished yet";
+    case DIALSORT_ERR_OVERFLOW: return "sum(H) exceeds the output capacity";
+    case DIALSORT_ERR_WORKSPACE: return "workspace too small or misaligned";
+  }
+  return "unknown status";
+}
+
+int dialsort_device_sm_count(void) {
+  const DeviceInfo* dev = device_info();
+  return dev ? dev->sms : 0;
+}
+
+const char* dialsort_version(void) { return "dialsort-gb300 0.1.0 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+// Host-side declarations shared by the translation units of libdialsort.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dialsort.h"
+
+namespace dialsort {
+
+struct DeviceInfo {
+  int device = -1;
+  int sms = 0;
+  size_t smem_optin = 0;  // max dynamic shared memory per CTA (opt-in)
+  uint32_t* err = nullptr;  // device address of the per-device error word
+};
+
+// Per-device properties and error word; initialised once per device, with
+// that device current.  Returns nullptr when no device is usable.
+const DeviceInfo* device_info();
+
+// Fully resolved launch choices for step 1.
+struct HistPlan {
+  uint32_t regime = DIALSORT_REGIME_GLOBAL_CRN;
+  bool crn = true;
+  uint32_t blocks = 0;
+  uint32_t threads = 1024;
+  uint32_t replicas = 1;
+  uint32_t cluster = 1;
+  uint32_t words_per_copy = 0;  // 32-bit words per shared-memory sub-histogram copy
+  size_t smem_bytes = 0;        // dynamic shared memory per CTA
+};
+
+// Fills every field of a plan (the autotuner); cfg fields that are non-zero
+// are taken as given.  Returns INVALID_ARG when a forced choice cannot work.
+dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
+                                 const dialsort_hist_config_t* cfg, const DeviceInfo& dev, HistPlan* plan);
+
+// Step 1 kernels (H must already be zero).  hist.cu
+cudaError_t launch_histogram(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
+                             const HistPlan& plan, uint32_t* err, cudaStream_t stream);
+
+// Step 2.  reconstruct.cu
+constexpr uint32_t kChunkBins = 1024;  // bins per offset-scan chunk
+constexpr uint32_t kTileKeys = 8192;   // output keys per expansion tile
+
+struct ReconLayout {
+  uint64_t num_chunks = 0, num_tiles = 0;
+  size_t off_ticket = 0, off_desc = 0, off_offsets = 0, off_first = 0;
+  size_t clear_bytes = 0;  // bytes at the start of the workspace zeroed before each scan
+  size_t total = 0;
+};
+ReconLayout recon_layout(uint32_t U, uint64_t n);
+
+cudaError_t launch_offsets(const uint32_t* H, uint32_t U, uint64_t n, void* ws, const ReconLayout& L,
+                           uint32_t* err, cudaStream_t stream);
+cudaError_t launch_expand(const uint32_t* H, uint32_t U, uint64_t n, void* out, uint32_t out_bytes, void* ws,
+                          const ReconLayout& L, cudaStream_t stream);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace dialsort

@@ -1,0 +1,74 @@
+"""ctypes binding of libdialsort.so: the C ABI of include/dialsort.h, same names.
+
+Argument marshalling only.  Every step of the DialSort path runs in the
+library's CUDA kernels; there is no CPU fallback.  Loading fails loudly when
+the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdialsort.so")
+
+P = ctypes.c_void_p
+U64 = ctypes.c_uint64
+U32 = ctypes.c_uint32
+SZ = ctypes.c_size_t
+INT = ctypes.c_int
+STATUS = ctypes.c_int
+
+
+class dialsort_hist_config_t(ctypes.Structure):
+    _fields_ = [("regime", U32), ("crn", U32), ("blocks", U32), ("threads", U32), ("replicas", U32),
+                ("cluster", U32)]
+
+
+# name -> (restype, argtypes); mirrors include/dialsort.h
+SIGNATURES = {
+    "dialsort_histogram": (STATUS, [P, U64, U32, P, P]),
+    "dialsort_histogram_u16": (STATUS, [P, U64, U32, P, P]),
+    "dialsort_histogram_ex": (STATUS, [P, U32, U64, U32, P, P, P]),
+    "dialsort_plan_histogram": (STATUS, [U64, U32, U32, U32, P]),
+    "dialsort_reconstruct_workspace_size": (SZ, [U32, U64]),
+    "dialsort_reconstruct": (STATUS, [P, U32, P, U64, P, SZ, P]),
+    "dialsort_reconstruct_u16": (STATUS, [P, U32, P, U64, P, SZ, P]),
+    "dialsort_offsets": (STATUS, [P, U32, U64, P, SZ, P]),
+    "dialsort_read_chunk_offsets": (STATUS, [P, U32, U64, P, P]),
+    "dialsort_sort_workspace_size": (SZ, [U64, U32]),
+    "dialsort_sort": (STATUS, [P, U64, U32, P, P, SZ, P]),
+    "dialsort_sort_u16": (STATUS, [P, U64, U32, P, P, SZ, P]),
+    "dialsort_sort_histogram": (P, [P]),
+    "dialsort_stream_status": (STATUS, [P, INT]),
+    "dialsort_status_string": (ctypes.c_char_p, [STATUS]),
+    "dialsort_device_sm_count": (INT, []),
+    "dialsort_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libdialsort.so and attach the signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: run `python -c 'import __graft_entry__ as g; g.build()'` first "
+                           "(DialSort has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def __getattr__(name):
+    # native.dialsort_histogram(...) etc. resolve to the C functions
+    if name.startswith("dialsort_"):
+        return getattr(load(), name)
+    raise AttributeError(name)
