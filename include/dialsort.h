@@ -137,6 +137,33 @@ dialsort_status_t dialsort_offsets(const uint32_t* H, uint32_t U, uint64_t n, vo
 dialsort_status_t dialsort_read_chunk_offsets(const void* ws, uint32_t U, uint64_t n, uint64_t* chunk_offsets,
                                               void* stream);
 
+/*
+ * Allocation-free variant of dialsort_reconstruct (uint32 output).  The paper
+ * has no counterpart: this exists for callers that cannot allocate device
+ * memory at call time -- e.g. a plugin that a host framework hands only its
+ * input and output buffers, or a latency-critical loop that must not take an
+ * allocator's locks or risk running out of memory mid-run.  The caller passes
+ * H and out exactly as for dialsort_reconstruct but no workspace.
+ *
+ * Scratch lives in a library-owned device array of
+ * DIALSORT_NOALLOC_SCRATCH_BYTES (2 MiB) on every device that loads the
+ * library, held until the process exits.  Sizes whose scratch would exceed it
+ * (dialsort_reconstruct_workspace_size(U, n) > DIALSORT_NOALLOC_SCRATCH_BYTES;
+ * every U <= 2^26 with n <= 2^30 fits) are rejected with
+ * DIALSORT_ERR_WORKSPACE before anything is launched.  The call allocates
+ * nothing (no cudaMalloc, no allocating library routine).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array: each call clears the parts that must start at zero, in stream order,
+ * but calls whose kernels overlap on the GPU (other streams or threads) race
+ * on it and must be serialised by the caller.
+ */
+#define DIALSORT_NOALLOC_SCRATCH_BYTES ((size_t)2 << 20)
+dialsort_status_t dialsort_reconstruct_noalloc(const uint32_t* H, uint32_t U, uint32_t* out, uint64_t n,
+                                               void* stream);
+
 /* ---------------------------------------------------------------- both steps */
 
 /* Bytes of workspace dialsort_sort needs: H (4U bytes) plus the scan scratch. */

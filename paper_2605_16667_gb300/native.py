@@ -36,6 +36,7 @@ SIGNATURES = {
     "dialsort_reconstruct_u16": (STATUS, [P, U32, P, U64, P, SZ, P]),
     "dialsort_offsets": (STATUS, [P, U32, U64, P, SZ, P]),
     "dialsort_read_chunk_offsets": (STATUS, [P, U32, U64, P, P]),
+    "dialsort_reconstruct_noalloc": (STATUS, [P, U32, P, U64, P]),
     "dialsort_sort_workspace_size": (SZ, [U64, U32]),
     "dialsort_sort": (STATUS, [P, U64, U32, P, P, SZ, P]),
     "dialsort_sort_u16": (STATUS, [P, U64, U32, P, P, SZ, P]),
