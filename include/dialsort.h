@@ -68,7 +68,8 @@ typedef enum {
 /* Launch choices for step 1.  Zero in any field means "pick automatically". */
 typedef struct {
   uint32_t regime;   /* dialsort_regime_t */
-  uint32_t crn;      /* 0 = auto, 1 = warp CRN on, 2 = off (the per-thread run merge always runs) */
+  uint32_t crn;      /* 0 = auto, 1 = warp CRN on, 2 = off, 3 = adaptive per warp (the per-thread run
+                        merge always runs; auto = adaptive, or off for REGIME_GLOBAL) */
   uint32_t blocks;   /* grid size */
   uint32_t threads;  /* CTA size: 256, 512 or 1024 */
   uint32_t replicas; /* shared-memory sub-histogram copies per CTA (SMEM32 / SMEM16) */

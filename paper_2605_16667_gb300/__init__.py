@@ -79,6 +79,8 @@ def _config(config) -> ctypes.c_void_p | None:
             v = REGIMES[v]
         if k == "crn" and isinstance(v, bool):
             v = 1 if v else 2
+        if k == "crn" and v == "adaptive":
+            v = 3
         setattr(c, k, int(v))
     return c
 

@@ -132,7 +132,8 @@ dialsort_status_t dialsort_plan_histogram(uint64_t n, uint32_t U, uint32_t key_b
   dialsort_hist_config_t in = *cfg;
   dialsort_status_t s = plan_histogram(n, U, key_bytes, skew_hint, &in, dev ? *dev : fallback, &p);
   if (s != DIALSORT_OK) return s;
-  *cfg = dialsort_hist_config_t{p.regime, p.crn ? 1u : 2u, p.blocks, p.threads, p.replicas, p.cluster};
+  const uint32_t crn_cfg = p.crn == 1 ? 1u : p.crn == 0 ? 2u : 3u;
+  *cfg = dialsort_hist_config_t{p.regime, crn_cfg, p.blocks, p.threads, p.replicas, p.cluster};
   return DIALSORT_OK;
 }
 

@@ -106,12 +106,23 @@ struct Vec<uint16_t> {
   }
 };
 
+enum CrnMode : uint32_t { CRN_OFF = 0, CRN_ON = 1, CRN_ADAPTIVE = 2 };
+
+// Adaptive CRN: a warp turns match.any on only while equal keys are common.
+// The probe is cheap -- how many lanes hold the same key as their left
+// neighbour -- and feeds a moving score (fixed point, decay 1/8) that is the
+// same in every lane, so the decision is warp-uniform.  The score settles at
+// 64 x (equal neighbours per round); the CRN is used from one per round on.
+// match.any costs about 30x an atomic when all 32 keys differ, and merges
+// hot keys when they do not.
+constexpr uint32_t kCrnScoreOn = 64;
+
 // Ingest the KPV keys one lane holds.  Must be called by all 32 lanes of the
 // warp together (the CRN step is a warp collective); lanes with valid == false
 // contribute nothing.
-template <int KPV, int MODE, bool CRN>
+template <int KPV, int MODE>
 __device__ __forceinline__ void ingest(const uint32_t (&k)[KPV], bool valid, const Sink<MODE>& s, uint32_t U,
-                                       bool& bad) {
+                                       bool& bad, uint32_t crn_mode, uint32_t& score) {
   // run length starting at each position (consecutive equal keys in the lane)
   uint32_t cnt[KPV];
   uint32_t run = 1;
@@ -126,24 +137,35 @@ __device__ __forceinline__ void ingest(const uint32_t (&k)[KPV], bool valid, con
     const bool in_range = k[j] < U;
     bad |= start && !in_range;
     const bool act = start && in_range;
-    if (CRN) {
-      const uint32_t m = __ballot_sync(0xffffffffu, act);
-      if (m == 0) continue;
+    if (crn_mode == CRN_OFF) {
+      if (act) s.add(k[j], cnt[j]);
+      continue;
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, act);
+    if (m == 0) continue;
+    bool use_crn = true;
+    if (crn_mode == CRN_ADAPTIVE) {
+      const uint32_t left = __shfl_up_sync(0xffffffffu, k[j], 1);
+      const uint32_t eq = __ballot_sync(0xffffffffu, act && left == k[j]) & (m << 1);
+      score = score - (score >> 3) + 8u * (uint32_t)__popc(eq);
+      use_crn = score >= kCrnScoreOn;
+    }
+    if (use_crn) {
       if (act) {
         const uint32_t peers = __match_any_sync(m, k[j]);
         const uint32_t total = __reduce_add_sync(peers, cnt[j]);
         if ((peers & lanemask_lt()) == 0) s.add(k[j], total);
       }
-    } else {
-      if (act) s.add(k[j], cnt[j]);
+    } else if (act) {
+      s.add(k[j], cnt[j]);
     }
   }
 }
 
-template <typename KeyT, int MODE, bool CRN>
+template <typename KeyT, int MODE>
 __global__ void __launch_bounds__(1024) hist_kernel(const KeyT* __restrict__ keys, uint64_t n, uint32_t U,
                                                     uint32_t* __restrict__ H, uint32_t* err, uint32_t replicas,
-                                                    uint32_t words_per_copy) {
+                                                    uint32_t words_per_copy, uint32_t crn_mode) {
   constexpr int KPV = Vec<KeyT>::K;
   constexpr int UNR = 4;
   extern __shared__ __align__(16) uint32_t sh[];
@@ -157,6 +179,7 @@ __global__ void __launch_bounds__(1024) hist_kernel(const KeyT* __restrict__ key
   }
   const Sink<MODE> s{sh + (warp % replicas) * words_per_copy, H, U};
   bool bad = false;
+  uint32_t score = 0;
 
   // scalar head up to the first 16-byte boundary, vector body, scalar tail
   const uint64_t mis = (reinterpret_cast<uintptr_t>(keys) & 15u) / sizeof(KeyT);
@@ -178,7 +201,7 @@ __global__ void __launch_bounds__(1024) hist_kernel(const KeyT* __restrict__ key
     for (int u = 0; u < UNR; ++u) {
       uint32_t k[KPV];
       Vec<KeyT>::unpack(q[u], k);
-      ingest<KPV, MODE, CRN>(k, v0 + u * stride + lane < nvec, s, U, bad);
+      ingest<KPV, MODE>(k, v0 + u * stride + lane < nvec, s, U, bad, crn_mode, score);
     }
   }
 
@@ -187,7 +210,7 @@ __global__ void __launch_bounds__(1024) hist_kernel(const KeyT* __restrict__ key
       const uint64_t i = i0 + lane;
       uint32_t k[1] = {0u};
       if (i < nscalar) k[0] = keys[i < head ? i : tail0 + (i - head)];
-      ingest<1, MODE, CRN>(k, i < nscalar, s, U, bad);
+      ingest<1, MODE>(k, i < nscalar, s, U, bad, crn_mode, score);
     }
   }
   if (bad) raise_error(err, ERRBIT_KEY_RANGE);
@@ -219,24 +242,23 @@ __global__ void __launch_bounds__(1024) hist_kernel(const KeyT* __restrict__ key
 
 namespace {
 
-
-template <typename KeyT, int MODE, bool CRN>
+template <typename KeyT, int MODE>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&hist_kernel<KeyT, MODE, CRN>);
+  return reinterpret_cast<const void*>(&hist_kernel<KeyT, MODE>);
 }
 
-const void* pick_kernel(uint32_t key_bytes, int mode, bool crn) {
+const void* pick_kernel(uint32_t key_bytes, int mode) {
   if (key_bytes == 4) {
     switch (mode) {
-      case MODE_SMEM32: return crn ? kernel_ptr<uint32_t, MODE_SMEM32, true>() : kernel_ptr<uint32_t, MODE_SMEM32, false>();
-      case MODE_SMEM16: return crn ? kernel_ptr<uint32_t, MODE_SMEM16, true>() : kernel_ptr<uint32_t, MODE_SMEM16, false>();
-      default: return crn ? kernel_ptr<uint32_t, MODE_GLOBAL, true>() : kernel_ptr<uint32_t, MODE_GLOBAL, false>();
+      case MODE_SMEM32: return kernel_ptr<uint32_t, MODE_SMEM32>();
+      case MODE_SMEM16: return kernel_ptr<uint32_t, MODE_SMEM16>();
+      default: return kernel_ptr<uint32_t, MODE_GLOBAL>();
     }
   }
   switch (mode) {
-    case MODE_SMEM32: return crn ? kernel_ptr<uint16_t, MODE_SMEM32, true>() : kernel_ptr<uint16_t, MODE_SMEM32, false>();
-    case MODE_SMEM16: return crn ? kernel_ptr<uint16_t, MODE_SMEM16, true>() : kernel_ptr<uint16_t, MODE_SMEM16, false>();
-    default: return crn ? kernel_ptr<uint16_t, MODE_GLOBAL, true>() : kernel_ptr<uint16_t, MODE_GLOBAL, false>();
+    case MODE_SMEM32: return kernel_ptr<uint16_t, MODE_SMEM32>();
+    case MODE_SMEM16: return kernel_ptr<uint16_t, MODE_SMEM16>();
+    default: return kernel_ptr<uint16_t, MODE_GLOBAL>();
   }
 }
 
@@ -252,13 +274,13 @@ int mode_of(uint32_t regime) {
 
 cudaError_t launch_histogram(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
                              const HistPlan& plan, uint32_t* err, cudaStream_t stream) {
-  const void* fn = pick_kernel(key_bytes, mode_of(plan.regime), plan.crn);
+  const void* fn = pick_kernel(key_bytes, mode_of(plan.regime));
   if (plan.smem_bytes > 48u * 1024u) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes);
     if (e != cudaSuccess) return e;
   }
-  uint32_t replicas = plan.replicas, wpc = plan.words_per_copy;
-  void* args[] = {const_cast<void**>(&keys), &n, &U, &H, &err, &replicas, &wpc};
+  uint32_t replicas = plan.replicas, wpc = plan.words_per_copy, crn = plan.crn;
+  void* args[] = {const_cast<void**>(&keys), &n, &U, &H, &err, &replicas, &wpc, &crn};
   return cudaLaunchKernel(fn, dim3(plan.blocks), dim3(plan.threads), args, plan.smem_bytes, stream);
 }
 
@@ -278,7 +300,7 @@ dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uin
   const uint32_t sms = dev.sms > 0 ? (uint32_t)dev.sms : 152u;
 
   if (c.threads != 0 && c.threads != 256 && c.threads != 512 && c.threads != 1024) return DIALSORT_ERR_INVALID_ARG;
-  if (c.crn > 2) return DIALSORT_ERR_INVALID_ARG;
+  if (c.crn > 3) return DIALSORT_ERR_INVALID_ARG;
 
   uint32_t regime = c.regime;
   if (regime == DIALSORT_REGIME_CLUSTER) return DIALSORT_ERR_INVALID_ARG;  // not built in this library version
@@ -296,7 +318,16 @@ dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uin
       regime = skew_hint == 1 ? DIALSORT_REGIME_GLOBAL : DIALSORT_REGIME_GLOBAL_CRN;
   }
   p.regime = regime;
-  p.crn = c.crn == 1 ? true : c.crn == 2 ? false : (regime != DIALSORT_REGIME_GLOBAL && skew_hint != 1);
+  // config: 0 auto, 1 on, 2 off, 3 adaptive.  Auto: adaptive, except off for the plain GLOBAL
+  // regime or when the caller says keys rarely repeat.
+  if (c.crn == 1)
+    p.crn = CRN_ON;
+  else if (c.crn == 2)
+    p.crn = CRN_OFF;
+  else if (c.crn == 3)
+    p.crn = CRN_ADAPTIVE;
+  else
+    p.crn = (regime == DIALSORT_REGIME_GLOBAL || skew_hint == 1) ? CRN_OFF : CRN_ADAPTIVE;
   p.threads = c.threads ? c.threads : 1024;
 
   if (regime == DIALSORT_REGIME_SMEM32 || regime == DIALSORT_REGIME_SMEM16) {

@@ -22,7 +22,7 @@ const DeviceInfo* device_info();
 // Fully resolved launch choices for step 1.
 struct HistPlan {
   uint32_t regime = DIALSORT_REGIME_GLOBAL_CRN;
-  bool crn = true;
+  uint32_t crn = 2;  // 0 off, 1 on, 2 adaptive (hist.cu CrnMode)
   uint32_t blocks = 0;
   uint32_t threads = 1024;
   uint32_t replicas = 1;

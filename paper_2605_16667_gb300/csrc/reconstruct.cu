@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kScanThreads) offsets_kernel(const uint32_t* _
 }
 
 template <typename OutT>
-__global__ void __launch_bounds__(kExpThreads) expand_kernel(const uint32_t* __restrict__ H, uint32_t U,
+__global__ void __launch_bounds__(kExpThreads, 6) expand_kernel(const uint32_t* __restrict__ H, uint32_t U,
                                                              uint64_t n_cap, uint64_t num_chunks,
                                                              const uint64_t* __restrict__ O,
                                                              const uint32_t* __restrict__ first_chunk,
@@ -182,76 +182,62 @@ __global__ void __launch_bounds__(kExpThreads) expand_kernel(const uint32_t* __r
   }
   __syncthreads();
 
-  // fill forward: every slot takes the latest mark at or before it
-  constexpr uint32_t PER = kTileKeys / kExpThreads;  // 32 slots per thread, contiguous
-  uint32_t v[PER];
-#pragma unroll
-  for (uint32_t q = 0; q < PER / 4; ++q) {
-    const uint4 x = M4[tid * (PER / 4) + q];
-    v[4 * q] = x.x;
-    v[4 * q + 1] = x.y;
-    v[4 * q + 2] = x.z;
-    v[4 * q + 3] = x.w;
-  }
-  uint32_t last = 0;
-#pragma unroll
-  for (uint32_t j = 0; j < PER; ++j) last = v[j] ? v[j] : last;
-  // inclusive "latest non-zero" scan over threads
-  uint32_t x = last;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-    if (lane >= (uint32_t)d && x == 0) x = y;
-  }
-  if (lane == 31) red32[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < kExpThreads / 32 ? red32[lane] : 0u;
-    uint32_t s = w;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
-      if (lane >= (uint32_t)d && s == 0) s = y;
+  // Fill forward: every slot takes the latest mark at or before it.  Warp w
+  // owns slots [1024 w, 1024 w + 1024); in round r lane l holds the quad at
+  // 1024 w + 128 r + 4 l, so shared-memory reads are conflict-free and each
+  // round's global store is 512 contiguous bytes.
+  constexpr uint32_t kWarpSlots = kTileKeys / (kExpThreads / 32);  // 1024
+  constexpr uint32_t kRounds = kWarpSlots / 128;                    // 8
+  const uint32_t wq = warp * (kWarpSlots / 4);                      // first quad of this warp
+  // pass 1: this warp's rightmost mark (scan rounds from the right)
+  uint32_t agg = 0;
+  for (int r = (int)kRounds - 1; r >= 0; --r) {
+    const uint4 q = M4[wq + r * 32 + lane];
+    const uint32_t last = q.w ? q.w : q.z ? q.z : q.y ? q.y : q.x;
+    const uint32_t bal = __ballot_sync(0xffffffffu, last != 0);
+    if (bal) {
+      agg = __shfl_sync(0xffffffffu, last, 31 - __clz(bal));
+      break;
     }
-    const uint32_t prev = __shfl_up_sync(0xffffffffu, s, 1);
-    if (lane < kExpThreads / 32) red32[lane] = lane ? prev : 0u;  // exclusive over warps
   }
+  if (lane == 0) red32[warp] = agg;
   __syncthreads();
-  uint32_t carry = __shfl_up_sync(0xffffffffu, x, 1);
-  if (lane == 0) carry = 0;
-  if (carry == 0) carry = red32[warp];
-#pragma unroll
-  for (uint32_t j = 0; j < PER; ++j) {
-    carry = v[j] ? v[j] : carry;
-    v[j] = carry - 1u;
-  }
-#pragma unroll
-  for (uint32_t q = 0; q < PER / 4; ++q)
-    M4[tid * (PER / 4) + q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-  __syncthreads();
+  uint32_t carry = 0;  // rightmost mark of the warps before this one
+  for (int w2 = (int)warp - 1; w2 >= 0 && carry == 0; --w2) carry = red32[w2];
 
   OutT* dst = out + tile_lo;
-  if (sizeof(OutT) == 4) {
-    uint32_t i = 0;
-    if (out_aligned) {
-      uint4* d4 = reinterpret_cast<uint4*>(dst);
-      const uint32_t quads = len / 4;
-      for (uint32_t qd = tid; qd < quads; qd += kExpThreads) d4[qd] = M4[qd];
-      i = quads * 4;
+  for (uint32_t r = 0; r < kRounds; ++r) {
+    const uint32_t slot = warp * kWarpSlots + r * 128 + lane * 4;
+    uint4 q = M4[wq + r * 32 + lane];
+    const uint32_t last = q.w ? q.w : q.z ? q.z : q.y ? q.y : q.x;
+    uint32_t x = last;  // inclusive "rightmost non-zero" over lanes
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= (uint32_t)d && x == 0) x = y;
     }
-    for (uint32_t k = i + tid; k < len; k += kExpThreads) dst[k] = (OutT)M[k];
-  } else {
-    uint32_t i = 0;
-    if (out_aligned) {
-      uint4* d4 = reinterpret_cast<uint4*>(dst);
-      const uint32_t octs = len / 8;
-      for (uint32_t o = tid; o < octs; o += kExpThreads) {
-        const uint4 a = M4[2 * o], b = M4[2 * o + 1];
-        d4[o] = make_uint4(a.x | (a.y << 16), a.z | (a.w << 16), b.x | (b.y << 16), b.z | (b.w << 16));
+    uint32_t c = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0 || c == 0) c = carry;
+    const uint32_t round_last = __shfl_sync(0xffffffffu, x, 31);
+    if (round_last) carry = round_last;
+    const uint32_t m0 = q.x ? q.x : c;
+    const uint32_t m1 = q.y ? q.y : m0;
+    const uint32_t m2 = q.z ? q.z : m1;
+    const uint32_t m3 = q.w ? q.w : m2;
+    q = make_uint4(m0 - 1u, m1 - 1u, m2 - 1u, m3 - 1u);  // marks hold key + 1
+    if (slot >= len) continue;
+    if (slot + 4 <= len && out_aligned) {
+      if (sizeof(OutT) == 4) {
+        *reinterpret_cast<uint4*>(dst + slot) = q;
+      } else {
+        *reinterpret_cast<uint2*>(dst + slot) = make_uint2(q.x | (q.y << 16), q.z | (q.w << 16));
       }
-      i = octs * 8;
+    } else {
+      dst[slot] = (OutT)q.x;
+      if (slot + 1 < len) dst[slot + 1] = (OutT)q.y;
+      if (slot + 2 < len) dst[slot + 2] = (OutT)q.z;
+      if (slot + 3 < len) dst[slot + 3] = (OutT)q.w;
     }
-    for (uint32_t k = i + tid; k < len; k += kExpThreads) dst[k] = (OutT)M[k];
   }
 }
 
@@ -294,6 +280,11 @@ cudaError_t launch_expand(const uint32_t* H, uint32_t U, uint64_t n, void* out, 
   const uint64_t* O = reinterpret_cast<const uint64_t*>(base + L.off_offsets);
   const uint32_t* first = reinterpret_cast<const uint32_t*>(base + L.off_first);
   const int aligned = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+  // 6 CTAs of 32 KB per SM need the large shared-memory carve-out
+  const void* fn = out_bytes == 4 ? reinterpret_cast<const void*>(&expand_kernel<uint32_t>)
+                                  : reinterpret_cast<const void*>(&expand_kernel<uint16_t>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
   if (out_bytes == 4)
     expand_kernel<uint32_t><<<(unsigned)L.num_tiles, kExpThreads, 0, stream>>>(
         H, U, n, L.num_chunks, O, first, static_cast<uint32_t*>(out), aligned);

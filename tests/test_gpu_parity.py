@@ -54,7 +54,7 @@ DISTS = ["uniform", "zipf", "all_equal", "sorted", "runs", "paper_skew", "zipf_p
 
 
 @pytest.mark.parametrize("regime,U", REGIME_CASES)
-@pytest.mark.parametrize("crn", [True, False])
+@pytest.mark.parametrize("crn", [True, False, "adaptive"])
 @pytest.mark.parametrize("width", [4, 2])
 @pytest.mark.parametrize("dist", DISTS)
 def test_histogram_every_regime(ds, regime, U, crn, width, dist):
@@ -90,7 +90,7 @@ def test_all_keys_at_universe_ends(ds, key, U):
 
 @pytest.mark.parametrize("U", [64, 63, 4097])
 @pytest.mark.parametrize("pattern", ["low_bin", "high_bin", "last_bin", "pair", "zipf"])
-@pytest.mark.parametrize("crn", [True, False])
+@pytest.mark.parametrize("crn", [True, False, "adaptive"])
 def test_smem16_carry_accounting(ds, U, pattern, crn):
     n = (1 << 19) + 7  # one CTA: every bin below would overflow 16 bits several times
     if pattern == "low_bin":
