@@ -182,6 +182,64 @@ dialsort_status_t dialsort_sort_u16(const uint16_t* keys, uint64_t n, uint32_t U
 /* Device pointer to the histogram that dialsort_sort leaves in ws. */
 uint32_t* dialsort_sort_histogram(void* ws);
 
+/* ---------------------------------------------------------------- batched form */
+
+/*
+ * One independent instance of a batch.  keys (n keys of key_bytes = 4 or 2),
+ * H (U uint32 counters, 16-byte aligned, overwritten) and out (n keys, or
+ * NULL for histogram only) are device pointers owned by the caller.  The same
+ * rules as for dialsort_histogram / dialsort_sort apply to each instance.
+ */
+typedef struct {
+  const void* keys;
+  uint32_t* H;
+  void* out;
+  uint64_t n;
+  uint32_t U;
+  uint32_t key_bytes;
+} dialsort_instance_t;
+
+/* A planned batch (host object).  Planning picks, per instance, how step 1
+ * privatises H (shared-memory 32-bit, packed 16-bit, or L2 atomics with the
+ * adaptive warp CRN), the keys per work item and the item counts of every
+ * phase, and orders instances largest first. */
+typedef struct dialsort_batch_s* dialsort_batch_t;
+
+/*
+ * Plans a batch of `count` instances.  With sort != 0 every instance with
+ * n > 0 needs out; with sort == 0 out is ignored (histograms only).  The
+ * instance array is copied; the device buffers it names must stay valid until
+ * the last launch of the batch has finished.
+ */
+dialsort_status_t dialsort_batch_create(const dialsort_instance_t* instances, uint32_t count, int sort,
+                                        dialsort_batch_t* batch);
+/* Workspace bytes (256-byte aligned device memory) a launch of the batch needs. */
+size_t dialsort_batch_workspace_size(dialsort_batch_t batch);
+/*
+ * Runs the whole batch on `stream`: two host-to-device copies of the plan
+ * tables (from pinned memory owned by the batch), two memsets and ONE
+ * persistent kernel whose CTAs pull work items of all instances.  Every call
+ * is asynchronous and can be captured into a CUDA graph (the graph reads the
+ * batch's pinned tables when it runs, so the batch must outlive the graph).
+ * Kernel-side errors (a key >= U, a wait that timed out) go to the error word.
+ */
+dialsort_status_t dialsort_batch_launch(dialsort_batch_t batch, void* ws, size_t ws_bytes, void* stream);
+/* Frees the batch's host tables (after its launches have finished). */
+dialsort_status_t dialsort_batch_destroy(dialsort_batch_t batch);
+/* The plan of instance `index` (caller's order): regime etc. in *cfg, and the
+ * item counts of the zero / histogram / offsets / expand phases in items[4]. */
+dialsort_status_t dialsort_batch_describe(dialsort_batch_t batch, uint32_t index, dialsort_hist_config_t* cfg,
+                                          uint32_t* items);
+
+/* One-shot forms: plan, launch, synchronise `stream`, free the plan. */
+size_t dialsort_batched_workspace_size(const dialsort_instance_t* instances, uint32_t count, int sort);
+dialsort_status_t dialsort_batched(const dialsort_instance_t* instances, uint32_t count, int sort, void* ws,
+                                   size_t ws_bytes, void* stream);
+dialsort_status_t dialsort_histogram_batched(const dialsort_instance_t* instances, uint32_t count, void* ws,
+                                             size_t ws_bytes, void* stream);
+dialsort_status_t dialsort_sort_batched(const dialsort_instance_t* instances, uint32_t count, void* ws,
+                                        size_t ws_bytes, void* stream);
+
 /* ---------------------------------------------------------------- status */
 
 /*

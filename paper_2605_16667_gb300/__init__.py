@@ -19,7 +19,7 @@ from . import native
 
 __all__ = [
     "DialSortError", "histogram", "reconstruct", "sort", "offsets", "plan_histogram", "stream_status",
-    "sort_workspace_size", "reconstruct_workspace_size", "REGIMES", "lib",
+    "sort_workspace_size", "reconstruct_workspace_size", "REGIMES", "lib", "Batch", "batched",
 ]
 
 OK, ERR_INVALID_ARG, ERR_KEY_RANGE, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_BUSY, ERR_OVERFLOW, ERR_WORKSPACE = range(9)
@@ -173,3 +173,70 @@ def plan_histogram(n: int, U: int, width: int = 4, skew_hint: int = 0, **forced)
     d = {f: getattr(c, f) for f, _ in c._fields_}
     d["regime_name"] = REGIME_NAMES[d["regime"]]
     return d
+
+
+class Batch:
+    """A planned batch of independent instances (dialsort_batch_*), run by one persistent launch.
+
+    keys: list of CUDA tensors (32- or 16-bit keys); U: list of universe sizes; H: list of int32
+    tensors (allocated when None); out: list of output tensors (allocated when sort and None).
+    """
+
+    def __init__(self, keys, U, H=None, out=None, *, sort: bool = True):
+        L = native.load()
+        n = len(keys)
+        self.keys = list(keys)
+        self.U = [int(u) for u in U]
+        self.sort = bool(sort)
+        dev = keys[0].device if n else torch.device("cuda")
+        self.H = list(H) if H is not None else [torch.empty(u, dtype=torch.int32, device=dev) for u in self.U]
+        if self.sort:
+            self.out = list(out) if out is not None else [torch.empty_like(k) for k in self.keys]
+        else:
+            self.out = [None] * n
+        arr = (native.dialsort_instance_t * max(n, 1))()
+        for i in range(n):
+            _cuda(self.keys[i], "keys")
+            _cuda(self.H[i], "H")
+            arr[i].keys = self.keys[i].data_ptr()
+            arr[i].H = self.H[i].data_ptr()
+            arr[i].out = self.out[i].data_ptr() if self.out[i] is not None else None
+            arr[i].n = self.keys[i].numel()
+            arr[i].U = self.U[i]
+            arr[i].key_bytes = _width(self.keys[i])
+        self._handle = ctypes.c_void_p()
+        _check(L.dialsort_batch_create(arr, n, 1 if self.sort else 0, ctypes.byref(self._handle)), "batch_create")
+        self.ws = torch.empty(max(L.dialsort_batch_workspace_size(self._handle), 256), dtype=torch.uint8,
+                              device=dev)
+
+    def launch(self, stream=None):
+        _check(native.load().dialsort_batch_launch(self._handle, self.ws.data_ptr(), self.ws.numel(), _stream(stream)),
+               "batch_launch")
+        return self
+
+    def describe(self, i: int) -> dict:
+        c = native.dialsort_hist_config_t()
+        items = (ctypes.c_uint32 * 4)()
+        _check(native.load().dialsort_batch_describe(self._handle, i, ctypes.byref(c), items), "batch_describe")
+        return {"regime_name": REGIME_NAMES[c.regime], "replicas": c.replicas, "items": list(items)}
+
+    def close(self):
+        if self._handle:
+            torch.cuda.synchronize()
+            native.load().dialsort_batch_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batched(keys, U, *, sort: bool = True, stream=None):
+    """One-shot batched run; returns (H list, out list)."""
+    b = Batch(keys, U, sort=sort)
+    b.launch(stream)
+    torch.cuda.current_stream().synchronize()
+    b.close()
+    return b.H, b.out

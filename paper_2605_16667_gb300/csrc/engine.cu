@@ -1,0 +1,548 @@
+// The request engine: one persistent kernel whose CTAs pull work items of many
+// independent DialSort requests (zero H, histogram a key range, one chunk of
+// the offset scan, one output tile of the projection) and move each request
+// through its phases.  It serves two forms:
+//
+//   batched  thousands of instances are planned on the host, uploaded, and
+//            run by ONE launch (memcpy + memset + kernel, so the whole batch
+//            can be captured in a CUDA graph); the kernel exits when every
+//            instance is finished.
+//   served   a host scheduler (serve.cu) admits requests into a ring of
+//            slots while the kernel runs; the kernel picks them up, finishes
+//            them out of order, and reports completions in host-mapped memory.
+//
+// Work search: each CTA looks at a window of up to 256 requests (one per
+// thread), takes the OLDEST request that still has unclaimed items in its
+// current phase, and claims an item with an atomic counter.  Items of a phase
+// are claimed in order, which is what the decoupled look-back of the offsets
+// phase needs (every earlier chunk is already held by a running CTA).  The
+// CTA that finishes a phase's last item publishes the next phase (release
+// store after a fence), so later phases see every write of earlier ones.
+// Every wait is bounded in time (%globaltimer): an idle CTA sleeps and gives
+// up after `idle_ns`, recording ERRBIT_TIMEOUT in batched mode.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "engine.h"
+#include "hist_device.cuh"
+#include "recon_device.cuh"
+
+namespace dialsort {
+namespace eng {
+
+namespace {
+
+enum Cmd : uint32_t { CMD_WORK = 0, CMD_RETRY = 1, CMD_SLEEP = 2, CMD_EXIT = 3 };
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+
+__device__ __forceinline__ uint32_t next_phase(const Req& r, uint32_t ph) {
+  for (uint32_t p = ph + 1; p <= PH_EXPAND; ++p)
+    if (r.count[p - 1]) return p;
+  return PH_DONE;
+}
+
+__device__ void zero_item(const Req& r, uint32_t item) {
+  const uint64_t w0 = (uint64_t)item * kZeroWords;
+  const uint64_t w1 = min(w0 + kZeroWords, (uint64_t)r.U);
+  uint4* H4 = reinterpret_cast<uint4*>(r.H);
+  const uint64_t q1 = w1 / 4;
+  for (uint64_t q = w0 / 4 + threadIdx.x; q < q1; q += blockDim.x) H4[q] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint64_t w = q1 * 4 + threadIdx.x; w < w1; w += blockDim.x) r.H[w] = 0u;
+}
+
+template <typename KeyT, int MODE>
+__device__ void hist_item(const Req& r, uint32_t item, uint32_t* sh, uint32_t* err, State* st) {
+  const uint64_t begin = (uint64_t)item * r.item_keys;
+  const uint64_t end = min(begin + r.item_keys, r.n);
+  const uint32_t warp = threadIdx.x >> 5;
+  if (MODE != MODE_GLOBAL) {
+    zero_smem(sh, r.replicas * r.words_per_copy);
+    __syncthreads();
+  }
+  const Sink<MODE> s{sh + (warp % r.replicas) * r.words_per_copy, r.H, r.U};
+  bool bad = false;
+  ingest_span<KeyT, MODE>(static_cast<const KeyT*>(r.keys) + begin, end - begin, r.U, s, warp * 32u, blockDim.x,
+                          true, r.crn, bad);
+  if (bad) {
+    raise_error(err, ERRBIT_KEY_RANGE);
+    atomicOr(&st->err, ERRBIT_KEY_RANGE);
+  }
+  if (MODE != MODE_GLOBAL) {
+    __syncthreads();
+    flush_smem<MODE>(sh, r.replicas, r.words_per_copy, r.U, r.H, r.owned != 0);
+  }
+}
+
+__device__ void run_hist(const Req& r, uint32_t item, uint32_t* sh, uint32_t* err, State* st) {
+  if (r.key_bytes == 4) {
+    if (r.mode == MODE_SMEM32)
+      hist_item<uint32_t, MODE_SMEM32>(r, item, sh, err, st);
+    else if (r.mode == MODE_SMEM16)
+      hist_item<uint32_t, MODE_SMEM16>(r, item, sh, err, st);
+    else
+      hist_item<uint32_t, MODE_GLOBAL>(r, item, sh, err, st);
+  } else {
+    if (r.mode == MODE_SMEM32)
+      hist_item<uint16_t, MODE_SMEM32>(r, item, sh, err, st);
+    else if (r.mode == MODE_SMEM16)
+      hist_item<uint16_t, MODE_SMEM16>(r, item, sh, err, st);
+    else
+      hist_item<uint16_t, MODE_GLOBAL>(r, item, sh, err, st);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  __shared__ uint64_t s_best[kThreads / 32];
+  __shared__ uint32_t s_prefix[kThreads / 32];
+  __shared__ uint32_t s_base, s_slot, s_ph, s_item, s_cmd, s_exit;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  uint64_t idle_since = 0;  // thread 0 only
+
+  for (;;) {
+    // ---- find the oldest request with an unclaimed item, claim one.  The
+    // first barrier makes sure every thread has read last round's shared words
+    // before thread 0 rewrites them.
+    __syncthreads();
+    if (tid == 0) {
+      s_base = L.served ? 0u : ld_volatile_u32(&L.ctl->tail);
+      s_cmd = CMD_SLEEP;
+    }
+    __syncthreads();
+    if (!L.served && s_base >= L.count) break;  // every request is finished
+    for (uint32_t wb = s_base; wb < L.count; wb += kWindow) {
+      const uint32_t len = min(kWindow, L.count - wb);
+      uint64_t key = ~0ull;
+      bool done = true;
+      if (tid < len) {
+        const uint32_t slot = wb + tid;
+        const uint32_t ph = ld_acquire_u32(&L.st[slot].phase);
+        done = (ph == PH_DONE);
+        if (ph >= PH_ZERO && ph <= PH_EXPAND &&
+            ld_volatile_u32(&L.st[slot].next[ph - 1]) < L.reqs[slot].count[ph - 1]) {
+          const uint64_t seq = L.served ? *(volatile uint64_t*)&L.st[slot].seq : (uint64_t)slot;
+          key = (seq << 8) | tid;
+        }
+      }
+      const uint32_t notdone = __ballot_sync(0xffffffffu, !done);
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        const uint64_t o = __shfl_xor_sync(0xffffffffu, key, d);
+        key = o < key ? o : key;
+      }
+      if (lane == 0) {
+        s_best[warp] = key;
+        s_prefix[warp] = notdone ? (uint32_t)(__ffs(notdone) - 1) : 32u;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        uint64_t best = ~0ull;
+        for (uint32_t w = 0; w < kThreads / 32; ++w) best = s_best[w] < best ? s_best[w] : best;
+        if (!L.served && wb == s_base) {
+          uint32_t pre = 0;  // finished requests at the front of the window
+          for (uint32_t w = 0; w < kThreads / 32; ++w) {
+            pre += s_prefix[w];
+            if (s_prefix[w] < 32u) break;
+          }
+          pre = min(pre, len);
+          if (pre) atomicMax(&L.ctl->tail, wb + pre);
+        }
+        if (best != ~0ull) {
+          const uint32_t slot = wb + (uint32_t)(best & 0xffu);
+          const uint32_t ph = ld_acquire_u32(&L.st[slot].phase);
+          s_cmd = CMD_RETRY;
+          if (ph >= PH_ZERO && ph <= PH_EXPAND) {
+            const uint32_t item = atomicAdd(&L.st[slot].next[ph - 1], 1u);
+            if (item < L.reqs[slot].count[ph - 1]) {
+              s_slot = slot;
+              s_ph = ph;
+              s_item = item;
+              s_cmd = CMD_WORK;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (s_cmd != CMD_SLEEP || L.served) break;  // served mode: the ring is one window
+    }
+
+    const uint32_t cmd = s_cmd;  // thread 0 writes it again only after the next loop-top barrier
+
+    // ---- nothing to do: wait (bounded), or leave
+    if (cmd == CMD_SLEEP) {
+      if (tid == 0) {
+        const uint64_t now = globaltimer();
+        if (idle_since == 0) idle_since = now;
+        s_exit = 0;
+        if (L.served && L.host->stop) {
+          s_exit = 1;
+        } else if (now - idle_since > L.idle_ns) {
+          if (!L.served) raise_error(L.err, ERRBIT_TIMEOUT);
+          s_exit = 1;
+        }
+      }
+      __syncthreads();
+      if (s_exit) break;
+      __nanosleep(2000);
+      continue;
+    }
+    if (cmd == CMD_RETRY) continue;
+    if (tid == 0) idle_since = 0;
+
+    // ---- do the item
+    const uint32_t slot = s_slot, ph = s_ph, item = s_item;
+    const Req& r = L.reqs[slot];
+    State* st = &L.st[slot];
+    switch (ph) {
+      case PH_ZERO:
+        zero_item(r, item);
+        break;
+      case PH_HIST:
+        run_hist(r, item, reinterpret_cast<uint32_t*>(dyn), L.err, st);
+        break;
+      case PH_OFFS:
+        offsets_chunk(r.H, r.U, r.n, r.count[PH_OFFS - 1], item, r.desc, r.O, r.first, L.err,
+                      *reinterpret_cast<OffsetsSmem*>(dyn));
+        break;
+      default:
+        if (r.key_bytes == 4)
+          expand_tile<uint32_t>(r.H, r.U, r.n, r.count[PH_OFFS - 1], r.O, r.first, static_cast<uint32_t*>(r.out),
+                                r.out_aligned, item, *reinterpret_cast<ExpandSmem*>(dyn));
+        else
+          expand_tile<uint16_t>(r.H, r.U, r.n, r.count[PH_OFFS - 1], r.O, r.first, static_cast<uint16_t*>(r.out),
+                                r.out_aligned, item, *reinterpret_cast<ExpandSmem*>(dyn));
+        break;
+    }
+
+    // ---- report; the last item of a phase publishes the next phase
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const uint32_t cnt = r.count[ph - 1];
+      if (atomicAdd(&st->done[ph - 1], 1u) + 1u == cnt) {
+        __threadfence();
+        const uint32_t np = next_phase(r, ph);
+        if (np == PH_DONE) {
+          const uint64_t t = globaltimer();
+          st->t_done = t;
+          if (L.served) {
+            Completion* c = &L.comp[slot];
+            c->err = ld_volatile_u32(&st->err);
+            c->t_done = t;
+            __threadfence_system();
+            c->seq_done = *(volatile uint64_t*)&st->seq + 1;
+          }
+        }
+        st_release_u32(&st->phase, np);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+void plan_request(const ReqPlanInput& in, Req* r) {
+  std::memset(r, 0, sizeof(Req));
+  r->keys = in.keys;
+  r->H = in.H;
+  r->out = in.out;
+  r->n = in.n;
+  r->U = in.U;
+  r->key_bytes = in.key_bytes;
+  r->crn = CRN_ADAPTIVE;
+  const uint64_t cap32 = kHistSmem / 4, cap16 = 2 * (kHistSmem / 4);
+  const uint64_t U = in.U, n = in.n;
+  if (n >= 2 * U && align_up(U, 4) <= cap32) {
+    r->mode = MODE_SMEM32;
+    r->words_per_copy = (uint32_t)align_up(U, 4);
+    uint32_t rep = 1;
+    while (rep < 8 && (uint64_t)r->words_per_copy * 4 * rep * 2 <= kHistSmem) rep *= 2;
+    r->replicas = rep;
+  } else if (n >= 2 * U && align_up((U + 1) / 2, 4) <= cap16 / 2) {
+    r->mode = MODE_SMEM16;
+    r->words_per_copy = (uint32_t)align_up((U + 1) / 2, 4);
+    r->replicas = 1;
+  } else {
+    r->mode = MODE_GLOBAL;
+    r->words_per_copy = 0;
+    r->replicas = 1;
+  }
+  if (r->mode == MODE_GLOBAL)
+    r->item_keys = 65536;
+  else
+    r->item_keys = align_up(std::max<uint64_t>(32768, 8ull * U * r->replicas), 8192);
+  const uint32_t n_hist = (uint32_t)((n + r->item_keys - 1) / r->item_keys);
+  r->owned = (r->mode == MODE_SMEM32 && n_hist == 1) ? 1u : 0u;
+  r->count[PH_ZERO - 1] = r->owned ? 0u : (uint32_t)((U + kZeroWords - 1) / kZeroWords);
+  r->count[PH_HIST - 1] = n_hist;
+  const bool sort = in.out != nullptr && n > 0;
+  r->count[PH_OFFS - 1] = sort ? (uint32_t)((U + kChunkBins - 1) / kChunkBins) : 0u;
+  r->count[PH_EXPAND - 1] = sort ? (uint32_t)((n + kTileKeys - 1) / kTileKeys) : 0u;
+  r->out_aligned = (reinterpret_cast<uintptr_t>(in.out) & 15u) == 0;
+  r->first_phase = PH_DONE;
+  for (uint32_t p = PH_ZERO; p <= PH_EXPAND; ++p)
+    if (r->count[p - 1]) {
+      r->first_phase = p;
+      break;
+    }
+}
+
+size_t request_scratch_bytes(const Req& r) {
+  const uint64_t chunks = r.count[PH_OFFS - 1], tiles = r.count[PH_EXPAND - 1];
+  if (chunks == 0) return 0;
+  return align_up(8 * chunks, 256) + align_up(8 * (chunks + 1), 256) + align_up(4 * std::max<uint64_t>(tiles, 1), 256);
+}
+
+void place_request_scratch(Req* r, char* base) {
+  const uint64_t chunks = r->count[PH_OFFS - 1];
+  if (chunks == 0) {
+    r->desc = nullptr;
+    r->O = nullptr;
+    r->first = nullptr;
+    return;
+  }
+  r->desc = reinterpret_cast<uint64_t*>(base);
+  base += align_up(8 * chunks, 256);
+  r->O = reinterpret_cast<uint64_t*>(base);
+  base += align_up(8 * (chunks + 1), 256);
+  r->first = reinterpret_cast<uint32_t*>(base);
+}
+
+size_t engine_smem_bytes() { return std::max<size_t>(kHistSmem, sizeof(ExpandSmem)); }
+
+namespace {
+constexpr int kMaxDev = 64;
+std::once_flag g_engine_once[kMaxDev];
+uint32_t g_engine_grid[kMaxDev];
+cudaError_t g_engine_err[kMaxDev];
+
+// Kernel attributes and the resident grid, set up once per device (so later
+// launches, e.g. inside a stream capture, make no attribute calls).
+void engine_setup(const DeviceInfo& dev) {
+  std::call_once(g_engine_once[dev.device], [&dev] {
+    const size_t smem = engine_smem_bytes();
+    int per_sm = 0;
+    cudaError_t e = cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel, kThreads, smem);
+    g_engine_err[dev.device] = e;
+    g_engine_grid[dev.device] = (uint32_t)(dev.sms * std::max(per_sm, 1));
+  });
+}
+}  // namespace
+
+uint32_t engine_grid(const DeviceInfo& dev) {
+  engine_setup(dev);
+  return g_engine_grid[dev.device];
+}
+
+cudaError_t launch_engine(const Launch& L, uint32_t grid, cudaStream_t stream) {
+  const DeviceInfo* dev = device_info();
+  if (!dev) return cudaErrorNoDevice;
+  engine_setup(*dev);
+  if (g_engine_err[dev->device] != cudaSuccess) return g_engine_err[dev->device];
+  engine_kernel<<<grid, kThreads, engine_smem_bytes(), stream>>>(L);
+  return cudaGetLastError();
+}
+
+}  // namespace eng
+}  // namespace dialsort
+
+// ---------------------------------------------------------------- batched C ABI
+
+using namespace dialsort;
+using namespace dialsort::eng;
+
+struct dialsort_batch_s {
+  uint32_t count = 0;
+  std::vector<uint32_t> order;  // table position -> caller's instance index (largest work first)
+  std::vector<size_t> scratch_off;
+  Req* h_reqs = nullptr;        // pinned
+  State* h_states = nullptr;    // pinned
+  size_t off_reqs = 0, off_states = 0, off_ctl = 0, off_scratch = 0, scratch_bytes = 0, total = 0;
+  void* planned_ws = nullptr;   // workspace the request table was last pointed at
+};
+
+namespace {
+
+bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+dialsort_status_t check_instance(const dialsort_instance_t& x) {
+  if (x.key_bytes != 4 && x.key_bytes != 2) return DIALSORT_ERR_INVALID_ARG;
+  if (x.U == 0 || x.n >= (1ull << 32)) return DIALSORT_ERR_INVALID_ARG;
+  if (x.key_bytes == 2 && x.U > 65536u) return DIALSORT_ERR_INVALID_ARG;
+  if (x.n > 0 && (x.keys == nullptr || !aligned_to(x.keys, x.key_bytes))) return DIALSORT_ERR_INVALID_ARG;
+  if (x.H == nullptr || !aligned_to(x.H, 16)) return DIALSORT_ERR_INVALID_ARG;
+  if (x.out != nullptr && !aligned_to(x.out, x.key_bytes)) return DIALSORT_ERR_INVALID_ARG;
+  return DIALSORT_OK;
+}
+
+void free_batch(dialsort_batch_s* b) {
+  if (!b) return;
+  if (b->h_reqs) cudaFreeHost(b->h_reqs);
+  if (b->h_states) cudaFreeHost(b->h_states);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+dialsort_status_t dialsort_batch_create(const dialsort_instance_t* inst, uint32_t count, int sort,
+                                        dialsort_batch_t* out) {
+  if (out == nullptr || (count > 0 && inst == nullptr)) return DIALSORT_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (uint32_t i = 0; i < count; ++i) {
+    dialsort_status_t s = check_instance(inst[i]);
+    if (s != DIALSORT_OK) return s;
+    if (sort && inst[i].n > 0 && inst[i].out == nullptr) return DIALSORT_ERR_INVALID_ARG;
+  }
+  dialsort_batch_s* b = new (std::nothrow) dialsort_batch_s();
+  if (!b) return DIALSORT_ERR_INVALID_ARG;
+  b->count = count;
+  const size_t nreq = std::max<uint32_t>(count, 1);
+  if (cudaMallocHost(&b->h_reqs, sizeof(Req) * nreq) != cudaSuccess ||
+      cudaMallocHost(&b->h_states, sizeof(State) * nreq) != cudaSuccess) {
+    free_batch(b);
+    return DIALSORT_ERR_CUDA;
+  }
+  // plan every instance, then order the table by estimated work (largest first)
+  std::vector<Req> plans(count);
+  std::vector<double> cost(count);
+  for (uint32_t i = 0; i < count; ++i) {
+    ReqPlanInput in{inst[i].keys, inst[i].H, sort ? inst[i].out : nullptr, inst[i].n, inst[i].U, inst[i].key_bytes};
+    plan_request(in, &plans[i]);
+    cost[i] = (double)inst[i].n * inst[i].key_bytes * (sort ? 2.0 : 1.0) + 12.0 * inst[i].U;
+  }
+  b->order.resize(count);
+  for (uint32_t i = 0; i < count; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t a, uint32_t c) { return cost[a] > cost[c]; });
+  size_t off = 0;
+  b->off_reqs = off;
+  off = align_up(off + sizeof(Req) * nreq, 256);
+  b->off_states = off;
+  off = align_up(off + sizeof(State) * nreq, 256);
+  b->off_ctl = off;
+  off = align_up(off + sizeof(Ctl), 256);
+  b->off_scratch = off;
+  b->scratch_off.resize(count);
+  size_t s = 0;
+  for (uint32_t p = 0; p < count; ++p) {
+    b->h_reqs[p] = plans[b->order[p]];
+    b->scratch_off[p] = s;
+    s += request_scratch_bytes(b->h_reqs[p]);
+  }
+  b->scratch_bytes = s;
+  b->total = align_up(off + s, 256);
+  for (uint32_t p = 0; p < count; ++p) {
+    std::memset(&b->h_states[p], 0, sizeof(State));
+    b->h_states[p].phase = b->h_reqs[p].first_phase;
+    b->h_states[p].seq = p;
+  }
+  *out = b;
+  return DIALSORT_OK;
+}
+
+size_t dialsort_batch_workspace_size(dialsort_batch_t b) { return b ? b->total : 0; }
+
+dialsort_status_t dialsort_batch_launch(dialsort_batch_t b, void* ws, size_t ws_bytes, void* stream) {
+  if (b == nullptr || ws == nullptr || !aligned_to(ws, 256) || ws_bytes < b->total) return DIALSORT_ERR_WORKSPACE;
+  const DeviceInfo* dev = device_info();
+  if (!dev) return DIALSORT_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  if (b->planned_ws != ws) {
+    for (uint32_t p = 0; p < b->count; ++p) place_request_scratch(&b->h_reqs[p], base + b->off_scratch + b->scratch_off[p]);
+    b->planned_ws = ws;
+  }
+  if (b->count == 0) return DIALSORT_OK;
+  cudaError_t e = cudaMemcpyAsync(base + b->off_reqs, b->h_reqs, sizeof(Req) * b->count, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + b->off_states, b->h_states, sizeof(State) * b->count, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + b->off_ctl, 0, sizeof(Ctl), st);
+  if (e == cudaSuccess && b->scratch_bytes) e = cudaMemsetAsync(base + b->off_scratch, 0, b->scratch_bytes, st);
+  if (e != cudaSuccess) return DIALSORT_ERR_CUDA;
+  Launch L{};
+  L.reqs = reinterpret_cast<const Req*>(base + b->off_reqs);
+  L.st = reinterpret_cast<State*>(base + b->off_states);
+  L.ctl = reinterpret_cast<Ctl*>(base + b->off_ctl);
+  L.err = dev->err;
+  L.count = b->count;
+  L.served = 0;
+  L.idle_ns = 2000000000ull;
+  return launch_engine(L, engine_grid(*dev), st) == cudaSuccess ? DIALSORT_OK : DIALSORT_ERR_CUDA;
+}
+
+dialsort_status_t dialsort_batch_destroy(dialsort_batch_t b) {
+  free_batch(b);
+  return DIALSORT_OK;
+}
+
+dialsort_status_t dialsort_batch_describe(dialsort_batch_t b, uint32_t index, dialsort_hist_config_t* cfg,
+                                          uint32_t* items) {
+  if (b == nullptr || cfg == nullptr || index >= b->count) return DIALSORT_ERR_INVALID_ARG;
+  uint32_t p = 0;
+  while (p < b->count && b->order[p] != index) ++p;
+  const Req& r = b->h_reqs[p];
+  const uint32_t regime = r.mode == MODE_SMEM32 ? DIALSORT_REGIME_SMEM32
+                          : r.mode == MODE_SMEM16 ? DIALSORT_REGIME_SMEM16
+                                                  : DIALSORT_REGIME_GLOBAL_CRN;
+  *cfg = dialsort_hist_config_t{regime, 3u, 0u, kThreads, r.replicas, 1u};
+  if (items)
+    for (int k = 0; k < 4; ++k) items[k] = r.count[k];
+  return DIALSORT_OK;
+}
+
+size_t dialsort_batched_workspace_size(const dialsort_instance_t* inst, uint32_t count, int sort) {
+  dialsort_batch_t b = nullptr;
+  if (dialsort_batch_create(inst, count, sort, &b) != DIALSORT_OK) return 0;
+  const size_t t = b->total;
+  free_batch(b);
+  return t;
+}
+
+dialsort_status_t dialsort_batched(const dialsort_instance_t* inst, uint32_t count, int sort, void* ws,
+                                   size_t ws_bytes, void* stream) {
+  dialsort_batch_t b = nullptr;
+  dialsort_status_t s = dialsort_batch_create(inst, count, sort, &b);
+  if (s != DIALSORT_OK) return s;
+  s = dialsort_batch_launch(b, ws, ws_bytes, stream);
+  // the host tables must outlive the asynchronous copies that read them
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess && s == DIALSORT_OK)
+    s = DIALSORT_ERR_CUDA;
+  free_batch(b);
+  return s;
+}
+
+dialsort_status_t dialsort_histogram_batched(const dialsort_instance_t* inst, uint32_t count, void* ws,
+                                             size_t ws_bytes, void* stream) {
+  return dialsort_batched(inst, count, 0, ws, ws_bytes, stream);
+}
+
+dialsort_status_t dialsort_sort_batched(const dialsort_instance_t* inst, uint32_t count, void* ws, size_t ws_bytes,
+                                        void* stream) {
+  return dialsort_batched(inst, count, 1, ws, ws_bytes, stream);
+}
+
+}  // extern "C"

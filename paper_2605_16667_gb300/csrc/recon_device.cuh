@@ -1,0 +1,234 @@
+// Device routines of step 2 (the ordered projection, Eq. (2)), shared by the
+// single-instance kernels (reconstruct.cu) and the batched/served engine
+// (engine.cu).  Each routine is executed by one 256-thread CTA.
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace dialsort {
+
+constexpr uint32_t kReconThreads = 256;  // threads of a CTA running these routines
+constexpr uint64_t kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62, kValMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ void load_bins4(const uint32_t* H, uint64_t b0, uint32_t U, uint32_t (&h)[4]) {
+  if (b0 + 3 < U) {
+    const uint4 q = *reinterpret_cast<const uint4*>(H + b0);
+    h[0] = q.x;
+    h[1] = q.y;
+    h[2] = q.z;
+    h[3] = q.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = (b0 + j < U) ? H[b0 + j] : 0u;
+  }
+}
+
+// Block-wide exclusive sum of one value per thread; returns the exclusive
+// prefix and writes the block total to *total.  `red` needs blockDim/32 + 1 slots.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_sum(T v, T* red, T* total) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= (uint32_t)d) x += y;
+  }
+  if (lane == 31) red[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < nw ? red[lane] : T(0);
+    T s = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, s, d);
+      if (lane >= (uint32_t)d) s += y;
+    }
+    if (lane < nw) red[lane] = s - w;  // exclusive prefix of warp totals
+    if (lane == nw - 1) red[nw] = s;
+  }
+  __syncthreads();
+  const T excl = red[warp] + (x - v);
+  *total = red[nw];
+  __syncthreads();  // red may be reused by the caller
+  return excl;
+}
+
+struct OffsetsSmem {
+  uint64_t red[kReconThreads / 32 + 1];
+  uint64_t excl;
+};
+
+// Chunk c of the offset scan: its total, its exclusive prefix by decoupled
+// look-back over desc[0..c), O[c] (and O[num_chunks] for the last chunk), and
+// the first chunk of every output tile whose first key falls in the chunk's
+// run range.  The caller guarantees that every chunk below c has already been
+// handed to a running CTA (tickets taken in order), so the look-back ends.
+__device__ __forceinline__ void offsets_chunk(const uint32_t* __restrict__ H, uint32_t U, uint64_t n_cap,
+                                              uint64_t num_chunks, uint64_t c, uint64_t* desc, uint64_t* O,
+                                              uint32_t* first_chunk, uint32_t* err, OffsetsSmem& sm) {
+  const uint32_t tid = threadIdx.x;
+  uint32_t h[4];
+  load_bins4(H, c * kChunkBins + tid * 4ull, U, h);
+  const uint64_t mine = (uint64_t)h[0] + h[1] + h[2] + h[3];
+  uint64_t agg;
+  block_exclusive_sum<uint64_t>(mine, sm.red, &agg);
+
+  if (tid == 0) {
+    uint64_t excl = 0;
+    if (c == 0) {
+      st_release_u64(desc, kFlagInc | (agg & kValMask));
+    } else {
+      st_release_u64(desc + c, kFlagAgg | (agg & kValMask));
+      // look back over predecessors until one has published its inclusive prefix
+      int64_t j = (int64_t)c - 1;
+      uint32_t spins = 0;
+      while (j >= 0) {
+        const uint64_t d = ld_acquire_u64(desc + j);
+        const uint64_t flag = d & ~kValMask;
+        if (flag == 0) {
+          if (++spins > kSpinLimit) {
+            raise_error(err, ERRBIT_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+          continue;
+        }
+        excl += d & kValMask;
+        if (flag == kFlagInc) break;
+        --j;
+      }
+      st_release_u64(desc + c, kFlagInc | ((excl + agg) & kValMask));
+    }
+    sm.excl = excl;
+    O[c] = excl;
+    if (c == num_chunks - 1) {
+      O[num_chunks] = excl + agg;
+      if (excl + agg > n_cap) raise_error(err, ERRBIT_OVERFLOW);
+    }
+  }
+  __syncthreads();
+  // tiles whose first key falls inside this chunk's run range [excl, excl + agg)
+  const uint64_t lo = sm.excl;
+  const uint64_t hi = min(lo + agg, n_cap);
+  if (agg != 0 && lo < hi) {
+    const uint64_t t0 = (lo + kTileKeys - 1) / kTileKeys;
+    const uint64_t t1 = (hi - 1) / kTileKeys;
+    for (uint64_t t = t0 + tid; t <= t1; t += kReconThreads) first_chunk[t] = (uint32_t)c;
+  }
+  __syncthreads();  // sm is reused by the caller's next item
+}
+
+struct ExpandSmem {
+  uint32_t M[kTileKeys];  // key + 1 where a run starts, 0 elsewhere
+  uint32_t red32[kReconThreads / 32 + 1];
+};
+
+// Output tile `tile` (keys [tile * 8192, ...)) of the projection.  Marks the
+// slot where each run starts (slot 0 gets the run covering the tile's first
+// key), fills forward ("latest mark wins"), and stores with 128-bit stores.
+template <typename OutT>
+__device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint32_t U, uint64_t n_cap,
+                                            uint64_t num_chunks, const uint64_t* __restrict__ O,
+                                            const uint32_t* __restrict__ first_chunk, OutT* __restrict__ out,
+                                            int out_aligned, uint64_t tile, ExpandSmem& sm) {
+  uint32_t* M = sm.M;
+  uint32_t* red32 = sm.red32;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint64_t total = min(O[num_chunks], n_cap);
+  const uint64_t tile_lo = tile * kTileKeys;
+  if (tile_lo >= total) return;
+  const uint64_t tile_hi = min(tile_lo + kTileKeys, total);
+  const uint32_t len = (uint32_t)(tile_hi - tile_lo);
+
+  uint4* M4 = reinterpret_cast<uint4*>(M);
+  for (uint32_t i = tid; i < kTileKeys / 4; i += kReconThreads) M4[i] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+
+  // mark run starts of every chunk overlapping [tile_lo, tile_hi)
+  for (uint64_t c = first_chunk[tile]; c < num_chunks; ++c) {
+    const uint64_t oc = O[c];
+    if (oc >= tile_hi) break;
+    if (O[c + 1] == oc) continue;  // empty chunk
+    uint32_t h[4];
+    const uint64_t b0 = c * kChunkBins + tid * 4ull;
+    load_bins4(H, b0, U, h);
+    uint32_t chunk_total;
+    uint32_t s = block_exclusive_sum<uint32_t>(h[0] + h[1] + h[2] + h[3], red32, &chunk_total);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (h[j] != 0) {
+        const uint64_t start = oc + s, end = start + h[j];
+        const uint32_t mark = (uint32_t)(b0 + j) + 1u;
+        if (start >= tile_lo && start < tile_hi)
+          M[start - tile_lo] = mark;
+        else if (start < tile_lo && end > tile_lo)
+          M[0] = mark;
+      }
+      s += h[j];
+    }
+  }
+  __syncthreads();
+
+  // Fill forward: every slot takes the latest mark at or before it.  Warp w
+  // owns slots [1024 w, 1024 w + 1024); in round r lane l holds the quad at
+  // 1024 w + 128 r + 4 l, so shared-memory reads are conflict-free and each
+  // round's global store is 512 contiguous bytes.
+  constexpr uint32_t kWarpSlots = kTileKeys / (kReconThreads / 32);  // 1024
+  constexpr uint32_t kRounds = kWarpSlots / 128;                      // 8
+  const uint32_t wq = warp * (kWarpSlots / 4);                        // first quad of this warp
+  // pass 1: this warp's rightmost mark (scan rounds from the right)
+  uint32_t agg = 0;
+  for (int r = (int)kRounds - 1; r >= 0; --r) {
+    const uint4 q = M4[wq + r * 32 + lane];
+    const uint32_t last = q.w ? q.w : q.z ? q.z : q.y ? q.y : q.x;
+    const uint32_t bal = __ballot_sync(0xffffffffu, last != 0);
+    if (bal) {
+      agg = __shfl_sync(0xffffffffu, last, 31 - __clz(bal));
+      break;
+    }
+  }
+  if (lane == 0) red32[warp] = agg;
+  __syncthreads();
+  uint32_t carry = 0;  // rightmost mark of the warps before this one
+  for (int w2 = (int)warp - 1; w2 >= 0 && carry == 0; --w2) carry = red32[w2];
+
+  OutT* dst = out + tile_lo;
+  for (uint32_t r = 0; r < kRounds; ++r) {
+    const uint32_t slot = warp * kWarpSlots + r * 128 + lane * 4;
+    uint4 q = M4[wq + r * 32 + lane];
+    const uint32_t last = q.w ? q.w : q.z ? q.z : q.y ? q.y : q.x;
+    uint32_t x = last;  // inclusive "rightmost non-zero" over lanes
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= (uint32_t)d && x == 0) x = y;
+    }
+    uint32_t c = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0 || c == 0) c = carry;
+    const uint32_t round_last = __shfl_sync(0xffffffffu, x, 31);
+    if (round_last) carry = round_last;
+    const uint32_t m0 = q.x ? q.x : c;
+    const uint32_t m1 = q.y ? q.y : m0;
+    const uint32_t m2 = q.z ? q.z : m1;
+    const uint32_t m3 = q.w ? q.w : m2;
+    q = make_uint4(m0 - 1u, m1 - 1u, m2 - 1u, m3 - 1u);  // marks hold key + 1
+    if (slot >= len) continue;
+    if (slot + 4 <= len && out_aligned) {
+      if (sizeof(OutT) == 4) {
+        *reinterpret_cast<uint4*>(dst + slot) = q;
+      } else {
+        *reinterpret_cast<uint2*>(dst + slot) = make_uint2(q.x | (q.y << 16), q.z | (q.w << 16));
+      }
+    } else {
+      dst[slot] = (OutT)q.x;
+      if (slot + 1 < len) dst[slot + 1] = (OutT)q.y;
+      if (slot + 2 < len) dst[slot + 2] = (OutT)q.z;
+      if (slot + 3 < len) dst[slot + 3] = (OutT)q.w;
+    }
+  }
+  __syncthreads();  // sm is reused by the caller's next item
+}
+
+}  // namespace dialsort

@@ -25,6 +25,10 @@ class dialsort_hist_config_t(ctypes.Structure):
                 ("cluster", U32)]
 
 
+class dialsort_instance_t(ctypes.Structure):
+    _fields_ = [("keys", P), ("H", P), ("out", P), ("n", U64), ("U", U32), ("key_bytes", U32)]
+
+
 # name -> (restype, argtypes); mirrors include/dialsort.h
 SIGNATURES = {
     "dialsort_histogram": (STATUS, [P, U64, U32, P, P]),
@@ -41,6 +45,15 @@ SIGNATURES = {
     "dialsort_sort": (STATUS, [P, U64, U32, P, P, SZ, P]),
     "dialsort_sort_u16": (STATUS, [P, U64, U32, P, P, SZ, P]),
     "dialsort_sort_histogram": (P, [P]),
+    "dialsort_batch_create": (STATUS, [P, U32, INT, P]),
+    "dialsort_batch_workspace_size": (SZ, [P]),
+    "dialsort_batch_launch": (STATUS, [P, P, SZ, P]),
+    "dialsort_batch_destroy": (STATUS, [P]),
+    "dialsort_batch_describe": (STATUS, [P, U32, P, P]),
+    "dialsort_batched_workspace_size": (SZ, [P, U32, INT]),
+    "dialsort_batched": (STATUS, [P, U32, INT, P, SZ, P]),
+    "dialsort_histogram_batched": (STATUS, [P, U32, P, SZ, P]),
+    "dialsort_sort_batched": (STATUS, [P, U32, P, SZ, P]),
     "dialsort_stream_status": (STATUS, [P, INT]),
     "dialsort_status_string": (ctypes.c_char_p, [STATUS]),
     "dialsort_device_sm_count": (INT, []),

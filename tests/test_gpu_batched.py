@@ -1,0 +1,134 @@
+"""Batched form: many uneven instances in one persistent launch, each bit-exact against the oracle
+and against the same instance run alone through the single-instance entry points."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ds():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2605_16667_gb300 as ds
+
+    return ds
+
+
+def dev(a, offset=0):
+    view = a.view(np.int32) if a.dtype == np.uint32 else a.view(np.int16)
+    buf = torch.empty(a.size + offset + 8, dtype=torch.int32 if a.dtype == np.uint32 else torch.int16, device="cuda")
+    t = buf[offset:offset + a.size]
+    t.copy_(torch.from_numpy(view.copy()))
+    return t
+
+
+def host(t, dtype):
+    return t.cpu().numpy().view(dtype)
+
+
+def make_instances(count, seed_stream, n_lo=4, n_hi=18, u_lo=1, u_hi=20, with_u16=True):
+    ns = gen.loguniform(count, n_lo, n_hi, stream=seed_stream)
+    us = gen.loguniform(count, u_lo, u_hi, stream=seed_stream + 1)
+    picks = gen.words(count, stream=seed_stream + 2)
+    inst = []
+    for i in range(count):
+        n, U = int(ns[i]), int(us[i])
+        width = 2 if (with_u16 and picks[i] % 4 == 0) else 4
+        if width == 2:
+            U = min(U, 65536)
+        dist = ["uniform", "zipf", "all_equal"][int(picks[i] >> 8) % 3]
+        keys = gen.keys(n, U, dist, width=width, stream=1000 + seed_stream * 8192 + i)
+        inst.append((keys, U))
+    # edge cases: empty, U = 1, a single key, unaligned keys
+    inst.append((np.zeros(0, dtype=np.uint32), 17))
+    inst.append((np.zeros(5000, dtype=np.uint32), 1))
+    inst.append((np.array([6], dtype=np.uint32), 7))
+    inst.append((gen.keys(12345, 999, "uniform", stream=7), 999))
+    return inst
+
+
+@pytest.mark.parametrize("sort", [True, False])
+def test_batch_matches_oracle_and_single_runs(ds, sort):
+    inst = make_instances(96, 50)
+    offsets = [(i % 3) for i in range(len(inst))]  # unaligned starts for a third of the instances
+    keys = [dev(k, o) for (k, _), o in zip(inst, offsets)]
+    U = [u for _, u in inst]
+    b = ds.Batch(keys, U, sort=sort).launch()
+    torch.cuda.synchronize()
+    assert ds.stream_status() == ds.OK
+    for i, (k, u) in enumerate(inst):
+        H_ref, _ = oracle.histogram(k, u)
+        np.testing.assert_array_equal(host(b.H[i], np.uint32), H_ref, err_msg=f"instance {i} n={k.size} U={u}")
+        if sort:
+            np.testing.assert_array_equal(host(b.out[i], k.dtype), oracle.reconstruct(H_ref, u, width=k.dtype.itemsize))
+            alone = ds.sort(keys[i], u)  # the same instance through the single-instance path
+            assert torch.equal(alone, b.out[i])
+    b.close()
+
+
+def test_batch_relaunch_and_plan_description(ds):
+    inst = make_instances(40, 60, with_u16=False)
+    keys = [dev(k) for k, _ in inst]
+    U = [u for _, u in inst]
+    b = ds.Batch(keys, U, sort=True)
+    for _ in range(3):  # the plan tables are re-uploaded each launch; results identical
+        for h in b.H:
+            h.fill_(-1)
+        b.launch()
+        torch.cuda.synchronize()
+        assert ds.stream_status() == ds.OK
+        for i, (k, u) in enumerate(inst):
+            np.testing.assert_array_equal(host(b.out[i], np.uint32), np.sort(k))
+    regimes = {b.describe(i)["regime_name"] for i in range(len(inst))}
+    assert regimes <= {"smem32", "smem16", "global_crn"}
+    b.close()
+
+
+def test_batch_captured_in_a_cuda_graph(ds):
+    inst = make_instances(48, 70, with_u16=False)
+    keys = [dev(k) for k, _ in inst]
+    U = [u for _, u in inst]
+    b = ds.Batch(keys, U, sort=True)
+    b.launch()  # first launch sets up kernel attributes outside the capture
+    torch.cuda.synchronize()
+    for o in b.out:
+        o.zero_()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            b.launch(stream=s)
+    torch.cuda.synchronize()
+    for o in b.out:
+        o.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert ds.stream_status() == ds.OK
+    for i, (k, u) in enumerate(inst):
+        np.testing.assert_array_equal(host(b.out[i], np.uint32), np.sort(k))
+    del g
+    b.close()
+
+
+def test_batch_reports_out_of_range_keys(ds):
+    good = gen.keys(10000, 100, "uniform", stream=80)
+    bad = good.copy()
+    bad[17] = 100
+    H, _ = ds.batched([dev(good), dev(bad)], [100, 100], sort=False)
+    assert ds.stream_status() == ds.ERR_KEY_RANGE
+    np.testing.assert_array_equal(host(H[1], np.uint32), oracle.histogram(bad, 100)[0])
+
+
+def test_empty_batch(ds):
+    H, out = ds.batched([], [], sort=True)
+    assert H == [] and out == []
