@@ -240,6 +240,91 @@ dialsort_status_t dialsort_histogram_batched(const dialsort_instance_t* instance
 dialsort_status_t dialsort_sort_batched(const dialsort_instance_t* instances, uint32_t count, void* ws,
                                         size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------- served form */
+
+/* Server configuration.  The server allocates, once at creation, an arena of
+ * hbm_budget_bytes of device memory for the H, output and scan scratch of
+ * admitted requests, plus small tables; nothing is allocated per request. */
+typedef struct {
+  uint64_t hbm_budget_bytes; /* arena size: admitted requests must fit in it together */
+  uint32_t max_slots;        /* requests on the device at once, 1..256 */
+  uint32_t reserved;
+  uint64_t idle_timeout_ns;  /* the device loop leaves after this long without work (0 = 20 ms) */
+} dialsort_server_cfg_t;
+
+/* A request: keys are a device pointer owned by the caller and must stay
+ * valid and unchanged until the request has finished. */
+typedef struct {
+  const void* keys;
+  uint64_t n;
+  uint32_t U;
+  uint32_t key_bytes; /* 4 or 2 */
+  uint32_t kind;      /* 0 = histogram (step 1), 1 = sort (steps 1 and 2) */
+  uint32_t reserved;
+} dialsort_request_t;
+
+/* A finished request.  H (U counters) and out (n sorted keys, kind 1 only)
+ * are device pointers into the server arena, valid until the ticket is
+ * released.  Times are CLOCK_MONOTONIC nanoseconds on the host: submission,
+ * admission to a device slot, and the moment the server saw it finish. */
+typedef struct {
+  uint32_t* H;
+  void* out;
+  uint64_t submit_ns, admit_ns, done_ns;
+  uint32_t status; /* DIALSORT_OK or a kernel-side error of this request */
+  uint32_t reserved;
+} dialsort_result_t;
+
+typedef struct dialsort_server_s dialsort_server_t;
+
+/* Starts a server on the current device: allocates the arena and tables,
+ * starts the scheduler thread.  The device loop is launched on demand. */
+dialsort_status_t dialsort_server_create(const dialsort_server_cfg_t* cfg, dialsort_server_t** server);
+/* Queues a request (admission is in arrival order, as slots and arena space
+ * free up).  DIALSORT_ERR_BUDGET if the request alone exceeds the arena. */
+dialsort_status_t dialsort_server_submit(dialsort_server_t* server, const dialsort_request_t* request,
+                                         uint64_t* ticket);
+/* DIALSORT_ERR_BUSY until the request has finished; then fills *result. */
+dialsort_status_t dialsort_server_poll(dialsort_server_t* server, uint64_t ticket, dialsort_result_t* result);
+/* As poll, blocking up to timeout_ns (DIALSORT_ERR_BUSY on timeout). */
+dialsort_status_t dialsort_server_wait(dialsort_server_t* server, uint64_t ticket, uint64_t timeout_ns,
+                                       dialsort_result_t* result);
+/* Returns a finished (or still pending) request's memory to the arena. */
+dialsort_status_t dialsort_server_release(dialsort_server_t* server, uint64_t ticket);
+/* Stops the scheduler, lets the device loop finish, frees everything. */
+dialsort_status_t dialsort_server_destroy(dialsort_server_t* server);
+
+/* A timed request stream, for comparing the served form with per-request
+ * plain launches on the same arrival trace. */
+typedef struct {
+  const void* keys;
+  uint64_t n;
+  uint32_t U;
+  uint32_t key_bytes;
+  uint32_t kind;
+  uint32_t reserved;
+  uint64_t arrival_ns; /* offset from the start of the replay */
+} dialsort_trace_entry_t;
+
+typedef struct {
+  uint64_t arrival_ns; /* as given */
+  uint64_t done_ns;    /* when the request was seen finished, same clock */
+  uint32_t status;
+  uint32_t reserved;
+} dialsort_trace_result_t;
+
+/*
+ * Replays `trace` in real time from the calling thread: with use_server != 0
+ * through a server created with *cfg (submit at each arrival, results
+ * released as they finish); otherwise with per-request plain launches
+ * (dialsort_histogram / dialsort_reconstruct on one stream at each arrival,
+ * memory from an arena of cfg->hbm_budget_bytes).  Fills results[i] and the
+ * replay's wall time.  Blocks until every request has finished.
+ */
+dialsort_status_t dialsort_replay(const dialsort_trace_entry_t* trace, uint32_t count, int use_server,
+                                  const dialsort_server_cfg_t* cfg, dialsort_trace_result_t* results,
+                                  uint64_t* wall_ns);
+
 /* ---------------------------------------------------------------- status */
 
 /*

@@ -19,7 +19,8 @@ from . import native
 
 __all__ = [
     "DialSortError", "histogram", "reconstruct", "sort", "offsets", "plan_histogram", "stream_status",
-    "sort_workspace_size", "reconstruct_workspace_size", "REGIMES", "lib", "Batch", "batched",
+    "sort_workspace_size", "reconstruct_workspace_size", "REGIMES", "lib", "Batch", "batched", "Server",
+    "replay", "device_view",
 ]
 
 OK, ERR_INVALID_ARG, ERR_KEY_RANGE, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_BUSY, ERR_OVERFLOW, ERR_WORKSPACE = range(9)
@@ -240,3 +241,98 @@ def batched(keys, U, *, sort: bool = True, stream=None):
     torch.cuda.current_stream().synchronize()
     b.close()
     return b.H, b.out
+
+
+class _CudaArray:
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def device_view(ptr: int, n: int, dtype: torch.dtype) -> torch.Tensor:
+    """A zero-copy tensor over n elements of device memory at ptr (memory owned elsewhere)."""
+    typestr = {torch.int32: "<i4", torch.int16: "<i2", torch.uint8: "|u1"}[dtype]
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_CudaArray(ptr, n, typestr), device="cuda")
+
+
+class Server:
+    """The served form (dialsort_server_*): continuous batching under an HBM budget."""
+
+    def __init__(self, hbm_budget_bytes: int = 1 << 30, max_slots: int = 64, idle_timeout_ns: int = 0):
+        cfg = native.dialsort_server_cfg_t(hbm_budget_bytes, max_slots, 0, idle_timeout_ns)
+        self._h = ctypes.c_void_p()
+        _check(native.load().dialsort_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "server_create")
+        self._keep = {}
+
+    def submit(self, keys: torch.Tensor, U: int, kind: str = "sort") -> int:
+        _cuda(keys, "keys")
+        r = native.dialsort_request_t(keys.data_ptr(), keys.numel(), U, _width(keys), 1 if kind == "sort" else 0, 0)
+        t = ctypes.c_uint64()
+        _check(native.load().dialsort_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "server_submit")
+        self._keep[t.value] = (keys, U, kind)  # keys must stay alive until the request finishes
+        return t.value
+
+    def _result(self, ticket, res):
+        keys, U, kind = self._keep[ticket]
+        w = _width(keys)
+        H = device_view(res.H, U, torch.int32)
+        out = device_view(res.out, keys.numel(), torch.int32 if w == 4 else torch.int16) if kind == "sort" else None
+        return {"H": H, "out": out, "status": res.status, "submit_ns": res.submit_ns, "admit_ns": res.admit_ns,
+                "done_ns": res.done_ns}
+
+    def poll(self, ticket: int):
+        res = native.dialsort_result_t()
+        st = native.load().dialsort_server_poll(self._h, ticket, ctypes.byref(res))
+        if st == ERR_BUSY:
+            return None
+        _check(st, "server_poll")
+        return self._result(ticket, res)
+
+    def wait(self, ticket: int, timeout_s: float = 30.0):
+        res = native.dialsort_result_t()
+        _check(native.load().dialsort_server_wait(self._h, ticket, int(timeout_s * 1e9), ctypes.byref(res)),
+               "server_wait")
+        return self._result(ticket, res)
+
+    def release(self, ticket: int):
+        _check(native.load().dialsort_server_release(self._h, ticket), "server_release")
+        self._keep.pop(ticket, None)
+
+    def close(self):
+        if self._h:
+            native.load().dialsort_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def replay(entries, *, use_server: bool, hbm_budget_bytes: int = 64 << 30, max_slots: int = 64,
+           idle_timeout_ns: int = 0):
+    """Replay a timed request trace (list of (keys tensor, U, kind, arrival_ns)); returns (results, wall_ns)."""
+    import numpy as np
+
+    n = len(entries)
+    arr = (native.dialsort_trace_entry_t * max(n, 1))()
+    for i, (keys, U, kind, t) in enumerate(entries):
+        arr[i].keys = keys.data_ptr()
+        arr[i].n = keys.numel()
+        arr[i].U = U
+        arr[i].key_bytes = _width(keys)
+        arr[i].kind = 1 if kind == "sort" else 0
+        arr[i].arrival_ns = int(t)
+    res = (native.dialsort_trace_result_t * max(n, 1))()
+    cfg = native.dialsort_server_cfg_t(hbm_budget_bytes, max_slots, 0, idle_timeout_ns)
+    wall = ctypes.c_uint64()
+    _check(native.load().dialsort_replay(arr, n, 1 if use_server else 0, ctypes.byref(cfg), res, ctypes.byref(wall)),
+           "replay")
+    out = np.zeros(n, dtype=[("arrival_ns", "u8"), ("done_ns", "u8"), ("status", "u4")])
+    for i in range(n):
+        out[i] = (res[i].arrival_ns, res[i].done_ns, res[i].status)
+    return out, wall.value

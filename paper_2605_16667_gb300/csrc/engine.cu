@@ -54,6 +54,37 @@ __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
 }
 
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+__device__ __forceinline__ uint64_t ld_volatile_u64(const unsigned long long* p) {
+  return *(const volatile unsigned long long*)p;
+}
+
+// Copy a request description into shared memory through L2 (never a stale
+// L1 line: in served mode the host rewrites a slot's description by DMA).
+__device__ __forceinline__ void load_req(const Req* src, Req* dst) {
+  static_assert(sizeof(Req) % 8 == 0, "Req is copied in 8-byte words");
+  const volatile unsigned long long* s = reinterpret_cast<const volatile unsigned long long*>(src);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+  for (uint32_t i = threadIdx.x; i < sizeof(Req) / 8; i += blockDim.x) d[i] = s[i];
+}
+
+// Claim the next item of phase ph of the request in `st` whose admission
+// sequence number is seq.  Returns the item index, or ~0u if none is left or
+// the slot no longer holds that request.
+__device__ __forceinline__ uint32_t claim_item(State* st, uint32_t ph, uint32_t count, uint64_t seq, bool served) {
+  unsigned long long* w = &st->claim[ph - 1];
+  if (!served) {
+    const uint32_t item = (uint32_t)atomicAdd(w, 1ull);
+    return item < count ? item : ~0u;
+  }
+  unsigned long long cur = ld_volatile_u64(w);
+  for (int tries = 0; tries < 64; ++tries) {
+    if ((uint32_t)(cur >> 32) != (uint32_t)seq || (uint32_t)cur >= count) return ~0u;
+    const unsigned long long prev = atomicCAS(w, cur, cur + 1ull);
+    if (prev == cur) return (uint32_t)cur;
+    cur = prev;
+  }
+  return ~0u;  // heavy contention: let the caller search again
+}
 
 __device__ __forceinline__ uint32_t next_phase(const Req& r, uint32_t ph) {
   for (uint32_t p = ph + 1; p <= PH_EXPAND; ++p)
@@ -116,8 +147,10 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
   __shared__ uint64_t s_best[kThreads / 32];
   __shared__ uint32_t s_prefix[kThreads / 32];
   __shared__ uint32_t s_base, s_slot, s_ph, s_item, s_cmd, s_exit;
+  __shared__ __align__(16) Req s_req;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   uint64_t idle_since = 0;  // thread 0 only
+  uint32_t backoff = 500;   // ns; doubles while idle (every thread keeps the same value)
 
   for (;;) {
     // ---- find the oldest request with an unclaimed item, claim one.  The
@@ -138,10 +171,11 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
         const uint32_t slot = wb + tid;
         const uint32_t ph = ld_acquire_u32(&L.st[slot].phase);
         done = (ph == PH_DONE);
-        if (ph >= PH_ZERO && ph <= PH_EXPAND &&
-            ld_volatile_u32(&L.st[slot].next[ph - 1]) < L.reqs[slot].count[ph - 1]) {
-          const uint64_t seq = L.served ? *(volatile uint64_t*)&L.st[slot].seq : (uint64_t)slot;
-          key = (seq << 8) | tid;
+        if (ph >= PH_ZERO && ph <= PH_EXPAND) {
+          const uint64_t seq = L.served ? ld_volatile_u64(&L.st[slot].seq) : (uint64_t)slot;
+          const uint64_t c = ld_volatile_u64(&L.st[slot].claim[ph - 1]);
+          const uint32_t cnt = ld_volatile_u32(&L.reqs[slot].count[ph - 1]);
+          if ((uint32_t)c < cnt && (uint32_t)(c >> 32) == (uint32_t)seq) key = (seq << 8) | tid;
         }
       }
       const uint32_t notdone = __ballot_sync(0xffffffffu, !done);
@@ -172,8 +206,9 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
           const uint32_t ph = ld_acquire_u32(&L.st[slot].phase);
           s_cmd = CMD_RETRY;
           if (ph >= PH_ZERO && ph <= PH_EXPAND) {
-            const uint32_t item = atomicAdd(&L.st[slot].next[ph - 1], 1u);
-            if (item < L.reqs[slot].count[ph - 1]) {
+            const uint32_t item = claim_item(&L.st[slot], ph, ld_volatile_u32(&L.reqs[slot].count[ph - 1]),
+                                             best >> 8, L.served != 0);
+            if (item != ~0u) {
               s_slot = slot;
               s_ph = ph;
               s_item = item;
@@ -203,15 +238,19 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
       }
       __syncthreads();
       if (s_exit) break;
-      __nanosleep(2000);
+      __nanosleep(backoff);
+      backoff = min(backoff * 2u, 16000u);
       continue;
     }
     if (cmd == CMD_RETRY) continue;
+    backoff = 500;
     if (tid == 0) idle_since = 0;
 
     // ---- do the item
     const uint32_t slot = s_slot, ph = s_ph, item = s_item;
-    const Req& r = L.reqs[slot];
+    load_req(&L.reqs[slot], &s_req);
+    __syncthreads();
+    const Req& r = s_req;
     State* st = &L.st[slot];
     switch (ph) {
       case PH_ZERO:
@@ -250,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
             c->err = ld_volatile_u32(&st->err);
             c->t_done = t;
             __threadfence_system();
-            c->seq_done = *(volatile uint64_t*)&st->seq + 1;
+            c->seq_done = ld_volatile_u64(&st->seq) + 1;
           }
         }
         st_release_u32(&st->phase, np);
@@ -459,6 +498,7 @@ dialsort_status_t dialsort_batch_create(const dialsort_instance_t* inst, uint32_
     std::memset(&b->h_states[p], 0, sizeof(State));
     b->h_states[p].phase = b->h_reqs[p].first_phase;
     b->h_states[p].seq = p;
+    for (int k = 0; k < 4; ++k) b->h_states[p].claim[k] = (unsigned long long)p << 32;
   }
   *out = b;
   return DIALSORT_OK;

@@ -40,14 +40,17 @@ struct Req {
 };
 
 // Mutable progress of one request (device memory).  `phase` is published last.
+// A claim word holds (low 32 bits of seq) << 32 | items handed out: in served
+// mode slots are reused, and a CTA claims with a compare-and-swap that fails
+// if the slot now holds a different request.
 struct State {
+  unsigned long long claim[4];  // per phase: zero, histogram, offsets, expand
+  unsigned long long seq;       // admission order (smaller = older = served first)
+  unsigned long long t_done;    // %globaltimer when the request finished
   uint32_t phase;
-  uint32_t next[4];   // items handed out, per phase
-  uint32_t done[4];   // items finished, per phase
-  uint32_t err;       // error bits of this request
-  uint64_t seq;       // admission order (smaller = older = served first)
-  uint64_t t_done;    // %globaltimer when the request finished
-  uint64_t pad[2];
+  uint32_t done[4];             // items finished, per phase
+  uint32_t err;                 // error bits of this request
+  uint32_t pad[2];
 };
 
 // Completion record in host-mapped memory (served mode).

@@ -29,6 +29,28 @@ class dialsort_instance_t(ctypes.Structure):
     _fields_ = [("keys", P), ("H", P), ("out", P), ("n", U64), ("U", U32), ("key_bytes", U32)]
 
 
+class dialsort_server_cfg_t(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", U64), ("max_slots", U32), ("reserved", U32), ("idle_timeout_ns", U64)]
+
+
+class dialsort_request_t(ctypes.Structure):
+    _fields_ = [("keys", P), ("n", U64), ("U", U32), ("key_bytes", U32), ("kind", U32), ("reserved", U32)]
+
+
+class dialsort_result_t(ctypes.Structure):
+    _fields_ = [("H", P), ("out", P), ("submit_ns", U64), ("admit_ns", U64), ("done_ns", U64), ("status", U32),
+                ("reserved", U32)]
+
+
+class dialsort_trace_entry_t(ctypes.Structure):
+    _fields_ = [("keys", P), ("n", U64), ("U", U32), ("key_bytes", U32), ("kind", U32), ("reserved", U32),
+                ("arrival_ns", U64)]
+
+
+class dialsort_trace_result_t(ctypes.Structure):
+    _fields_ = [("arrival_ns", U64), ("done_ns", U64), ("status", U32), ("reserved", U32)]
+
+
 # name -> (restype, argtypes); mirrors include/dialsort.h
 SIGNATURES = {
     "dialsort_histogram": (STATUS, [P, U64, U32, P, P]),
@@ -54,6 +76,13 @@ SIGNATURES = {
     "dialsort_batched": (STATUS, [P, U32, INT, P, SZ, P]),
     "dialsort_histogram_batched": (STATUS, [P, U32, P, SZ, P]),
     "dialsort_sort_batched": (STATUS, [P, U32, P, SZ, P]),
+    "dialsort_server_create": (STATUS, [P, P]),
+    "dialsort_server_submit": (STATUS, [P, P, P]),
+    "dialsort_server_poll": (STATUS, [P, U64, P]),
+    "dialsort_server_wait": (STATUS, [P, U64, U64, P]),
+    "dialsort_server_release": (STATUS, [P, U64]),
+    "dialsort_server_destroy": (STATUS, [P]),
+    "dialsort_replay": (STATUS, [P, U32, INT, P, P, P]),
     "dialsort_stream_status": (STATUS, [P, INT]),
     "dialsort_status_string": (ctypes.c_char_p, [STATUS]),
     "dialsort_device_sm_count": (INT, []),
