@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
+    p.add_argument("--served-seconds", type=float, default=10.0)
+    p.add_argument("--form", default="all", choices=["all", "batched", "served"],
+                   help="print only the batched or served form's measurement")
     # workload-size overrides, for profiling smaller cases of the same kernels
     p.add_argument("--n", type=int, default=N_KEYS)
     p.add_argument("--U", type=int, default=UNIVERSE)
@@ -155,6 +159,149 @@ def cpu_baseline(n_sample: int, runs_budget_s: float = 15.0):
                       f"projection, best of {len(times)} runs"}, times
 
 
+def _align(x, a):
+    return (x + a - 1) // a * a
+
+
+def run_batched(ds, torch, stream, reps: int = 3):
+    """4096 independent instances in one persistent launch vs per-request plain launches.
+
+    n_i log-uniform in [2^10, 2^22], U_i log-uniform in [2^8, 2^20], each instance's distribution
+    drawn uniformly from {uniform, Zipf s=1.2, all equal}; uint32 keys; histogram + projection.
+    """
+    import concurrent.futures
+
+    import gen
+
+    count = 4096
+    ns = gen.loguniform(count, 10, 22, stream=4 * 16).astype(np.int64)
+    us = gen.loguniform(count, 8, 20, stream=4 * 16 + 1).astype(np.int64)
+    picks = gen.words(count, stream=4 * 16 + 2)
+    dists = [["uniform", "zipf", "all_equal"][int(p % 3)] for p in picks]
+    koff = np.zeros(count + 1, dtype=np.int64)
+    hoff = np.zeros(count + 1, dtype=np.int64)
+    for i in range(count):
+        koff[i + 1] = koff[i] + _align(int(ns[i]), 64)
+        hoff[i + 1] = hoff[i] + _align(int(us[i]), 64)
+    host = np.empty(int(koff[-1]), dtype=np.uint32)
+
+    def fill(i):
+        gen.keys(int(ns[i]), int(us[i]), dists[i], stream=4 * 16 * 1000 + i,
+                 out=host[koff[i]:koff[i] + ns[i]])
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        list(ex.map(fill, range(count)))
+    keys_d = torch.from_numpy(host.view(np.int32)).cuda()
+    out_d = torch.empty_like(keys_d)
+    H_d = torch.empty(int(hoff[-1]), dtype=torch.int32, device="cuda")
+    kv = [keys_d[koff[i]:koff[i] + ns[i]] for i in range(count)]
+    ov = [out_d[koff[i]:koff[i] + ns[i]] for i in range(count)]
+    hv = [H_d[hoff[i]:hoff[i] + us[i]] for i in range(count)]
+    total_keys = int(ns.sum())
+    algo_bytes = int(8 * ns.sum() + 12 * us.sum())
+
+    b = ds.Batch(kv, [int(u) for u in us], H=hv, out=ov, sort=True)
+    b.launch(stream)
+    torch.cuda.synchronize()
+    ok = ds.stream_status() == ds.OK
+    # spot-check a few instances against numpy sort (outside any timing)
+    for i in (0, count // 2, count - 1):
+        ok = ok and bool(np.array_equal(ov[i].cpu().numpy().view(np.uint32), np.sort(host[koff[i]:koff[i] + ns[i]])))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        b.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1) / reps
+    # the same launch captured in a CUDA graph
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream()
+    with torch.cuda.stream(s2):
+        with torch.cuda.graph(g, stream=s2):
+            b.launch(s2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / reps
+    del g
+    b.close()
+    # per-request plain launches on one stream (C loop: all arrivals at t = 0)
+    entries = [(kv[i], int(us[i]), "sort", 0) for i in range(count)]
+    ds.replay(entries[:64], use_server=False, hbm_budget_bytes=8 << 30)  # warm-up
+    _, plain_wall = ds.replay(entries, use_server=False, hbm_budget_bytes=8 << 30)
+    plain_ms = plain_wall / 1e6
+    best = min(batched_ms, graph_ms)
+    return {"workload": "4096 instances, n_i log-uniform [2^10,2^22], U_i log-uniform [2^8,2^20], "
+                        "uniform/Zipf 1.2/all-equal, uint32, histogram + projection",
+            "total_keys": total_keys, "batched_ms": batched_ms, "graph_ms": graph_ms,
+            "plain_launches_ms": plain_ms, "batched_keys_per_s": total_keys / (best / 1e3),
+            "plain_keys_per_s": total_keys / (plain_ms / 1e3), "speedup_vs_plain": plain_ms / best,
+            "hbm_frac": algo_bytes / (best / 1e3) / 1e9 / peaks()[0], "algorithmic_bytes": algo_bytes,
+            "launches": 1, "checked": ok}
+
+
+def run_served(ds, torch, seconds: float = 10.0, warm: float = 1.0, rate: float = 2000.0):
+    """Poisson request stream through the server vs per-request plain launches (same trace).
+
+    n log-uniform [2^12,2^26], U log-uniform [2^8,2^24], uint32/uint16 keys 50/50 (uint16 => U <= 2^16),
+    sort/histogram 50/50, uniform/Zipf 1.2 50/50, 64 GB HBM budget.  Keys are pre-staged on the device:
+    for each (distribution, width) one base array of 2^26 keys drawn over the largest universe, and
+    for each power of two 2^c the keys shifted right so they lie in [0, 2^c); a request with universe
+    U reads a slice of the class floor(log2 U), so every key is < U.
+    """
+    import gen
+
+    count = int(rate * (seconds + warm))
+    gaps = -np.log1p(-gen.unit(count, stream=5 * 16)) / rate
+    arrivals = np.cumsum(gaps)
+    ns = gen.loguniform(count, 12, 26, stream=5 * 16 + 1).astype(np.int64)
+    us = gen.loguniform(count, 8, 24, stream=5 * 16 + 2).astype(np.int64)
+    w = gen.words(count, stream=5 * 16 + 3)
+    width = np.where(w & 1, 2, 4)
+    us = np.where(width == 2, np.minimum(us, 65536), us)
+    kind = np.where((w >> 1) & 1, "sort", "histogram")
+    dist = np.where((w >> 2) & 1, "zipf", "uniform")
+    pools = {}
+    for d in ("uniform", "zipf"):
+        for wd, top in ((4, 24), (2, 16)):
+            base = gen.keys(1 << 26, 1 << top, d, width=wd, param=1.2 if d == "zipf" else None, stream=5 * 16 + 8)
+            bt = torch.from_numpy(base.view(np.int32 if wd == 4 else np.int16)).cuda()
+            if wd == 2:
+                bt = bt.to(torch.int32) & 0xFFFF
+            for c in range(8, top + 1):
+                sh = (bt >> (top - c)).to(torch.int32 if wd == 4 else torch.int16)
+                pools[(d, wd, c)] = sh
+            del bt
+    offs = gen.words(count, stream=5 * 16 + 4)
+    entries = []
+    for i in range(count):
+        c = int(np.floor(np.log2(us[i])))
+        pool = pools[(str(dist[i]), int(width[i]), c)]
+        o = int(offs[i] % ((1 << 26) - ns[i] + 1))
+        o -= o % 8  # keep slices 16-byte aligned
+        entries.append((pool[o:o + ns[i]], int(us[i]), str(kind[i]), int(arrivals[i] * 1e9)))
+    meas = arrivals >= warm
+    out = {"workload": f"Poisson {rate:.0f} req/s for {seconds:.0f} s after {warm:.0f} s warm-up "
+                       f"({int(meas.sum())} measured requests), n log-uniform [2^12,2^26], U log-uniform "
+                       "[2^8,2^24], uint32/uint16, sort/histogram, uniform/Zipf 1.2, 64 GB budget",
+           "requests": int(meas.sum())}
+    for name, use_server in (("served", True), ("plain_launches", False)):
+        res, wall = ds.replay(entries, use_server=use_server, hbm_budget_bytes=64 << 30, max_slots=64)
+        lat = (res["done_ns"].astype(np.float64) - res["arrival_ns"].astype(np.float64))[meas] / 1e6
+        span = (res["done_ns"][meas].max() - res["arrival_ns"][meas].min()) / 1e9
+        st_vals, st_counts = np.unique(res["status"], return_counts=True)
+        out[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "mean_ms": float(lat.mean()), "keys_per_s": float(ns[meas].sum() / span),
+                     "all_ok": bool(np.all(res["status"] == 0)), "wall_s": wall / 1e9,
+                     "status_counts": {int(v): int(c) for v, c in zip(st_vals, st_counts)}}
+    del pools
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle on host cores, on this workload's config and metric (bounded sample per step)."""
     if rank != 0:
@@ -202,6 +349,12 @@ def main():
     import paper_2605_16667_gb300 as ds
 
     torch.cuda.set_device(local_rank)
+    if args.form != "all":
+        stream = torch.cuda.current_stream()
+        res = run_batched(ds, torch, stream) if args.form == "batched" else \
+            run_served(ds, torch, seconds=args.served_seconds)
+        print(json.dumps({"form": args.form, **res}), flush=True)
+        return 0
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -323,6 +476,16 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cpu, _ = cpu_baseline(1 << 25)
 
+    # the batched and served forms, each against per-request plain launches
+    forms = {}
+    if not args.no_forms and n == N_KEYS:
+        del keys, out, ws, rws, pin_in, pin_out, d_in
+        torch.cuda.empty_cache()
+        forms["batched"] = run_batched(ds, torch, stream)
+        torch.cuda.empty_cache()
+        forms["served"] = run_served(ds, torch, seconds=args.served_seconds)
+        torch.cuda.empty_cache()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
@@ -338,6 +501,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": 3 * args.steps, "status": status, "hist_sum_ok": hist_sum_ok, "sorted_ok": sorted_ok,
         }
+        line.update(forms)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -217,7 +217,7 @@ dialsort_status_t dialsort_batch_create(const dialsort_instance_t* instances, ui
 size_t dialsort_batch_workspace_size(dialsort_batch_t batch);
 /*
  * Runs the whole batch on `stream`: two host-to-device copies of the plan
- * tables (from pinned memory owned by the batch), two memsets and ONE
+ * tables (from pinned memory owned by the batch), one memset and ONE
  * persistent kernel whose CTAs pull work items of all instances.  Every call
  * is asynchronous and can be captured into a CUDA graph (the graph reads the
  * batch's pinned tables when it runs, so the batch must outlive the graph).

@@ -13,13 +13,16 @@
 //
 // Work search: each CTA looks at a window of up to 256 requests (one per
 // thread), takes the OLDEST request that still has unclaimed items in its
-// current phase, and claims an item with an atomic counter.  Items of a phase
-// are claimed in order, which is what the decoupled look-back of the offsets
-// phase needs (every earlier chunk is already held by a running CTA).  The
-// CTA that finishes a phase's last item publishes the next phase (release
-// store after a fence), so later phases see every write of earlier ones.
-// Every wait is bounded in time (%globaltimer): an idle CTA sleeps and gives
-// up after `idle_ns`, recording ERRBIT_TIMEOUT in batched mode.
+// current phase, and claims an item with one atomicAdd on the request's
+// state word (see State in engine.h: the returned word names the claimed
+// phase and item).  Items of a phase are claimed in order, which is what the
+// decoupled look-back of the offsets phase needs (every earlier chunk is
+// already held by a running CTA).  The CTA that finishes a phase's last item
+// publishes the next phase (exchange after a fence), so later phases see
+// every write of earlier ones.  Every wait is bounded in time (%globaltimer):
+// idle CTAs sleep with back-off and leave once the whole engine has had no
+// work for `idle_ns` (recording ERRBIT_TIMEOUT in batched mode, where that
+// can only mean something went wrong).
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -67,38 +70,33 @@ __device__ __forceinline__ void load_req(const Req* src, Req* dst) {
   for (uint32_t i = threadIdx.x; i < sizeof(Req) / 8; i += blockDim.x) d[i] = s[i];
 }
 
-// Claim the next item of phase ph of the request in `st` whose admission
-// sequence number is seq.  Returns the item index, or ~0u if none is left or
-// the slot no longer holds that request.
-__device__ __forceinline__ uint32_t claim_item(State* st, uint32_t ph, uint32_t count, uint64_t seq, bool served) {
-  unsigned long long* w = &st->claim[ph - 1];
-  if (!served) {
-    const uint32_t item = (uint32_t)atomicAdd(w, 1ull);
-    return item < count ? item : ~0u;
-  }
-  unsigned long long cur = ld_volatile_u64(w);
-  for (int tries = 0; tries < 64; ++tries) {
-    if ((uint32_t)(cur >> 32) != (uint32_t)seq || (uint32_t)cur >= count) return ~0u;
-    const unsigned long long prev = atomicCAS(w, cur, cur + 1ull);
-    if (prev == cur) return (uint32_t)cur;
-    cur = prev;
-  }
-  return ~0u;  // heavy contention: let the caller search again
-}
-
 __device__ __forceinline__ uint32_t next_phase(const Req& r, uint32_t ph) {
   for (uint32_t p = ph + 1; p <= PH_EXPAND; ++p)
     if (r.count[p - 1]) return p;
   return PH_DONE;
 }
 
+// The zero phase clears, in kZeroWords-word items, the concatenation of H
+// (when the histogram phase adds into it) and the look-back descriptors of
+// the offsets phase.  Doing this on the device keeps admission free of
+// kernels (a memset could not start while the engine occupies every SM).
+__device__ void zero_words(uint32_t* p, uint64_t w0, uint64_t w1) {  // p 16-byte aligned
+  uint64_t a = (w0 + 3) & ~3ull;
+  if (a > w1) a = w1;
+  const uint64_t b = a + ((w1 - a) & ~3ull);
+  for (uint64_t w = w0 + threadIdx.x; w < a; w += blockDim.x) p[w] = 0u;
+  uint4* p4 = reinterpret_cast<uint4*>(p);
+  for (uint64_t q = a / 4 + threadIdx.x; q < b / 4; q += blockDim.x) p4[q] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint64_t w = b + threadIdx.x; w < w1; w += blockDim.x) p[w] = 0u;
+}
+
 __device__ void zero_item(const Req& r, uint32_t item) {
+  const uint64_t h_words = r.zero_H ? (uint64_t)r.U : 0;
+  const uint64_t d_words = r.desc ? 2ull * r.count[PH_OFFS - 1] : 0;
   const uint64_t w0 = (uint64_t)item * kZeroWords;
-  const uint64_t w1 = min(w0 + kZeroWords, (uint64_t)r.U);
-  uint4* H4 = reinterpret_cast<uint4*>(r.H);
-  const uint64_t q1 = w1 / 4;
-  for (uint64_t q = w0 / 4 + threadIdx.x; q < q1; q += blockDim.x) H4[q] = make_uint4(0u, 0u, 0u, 0u);
-  for (uint64_t w = q1 * 4 + threadIdx.x; w < w1; w += blockDim.x) r.H[w] = 0u;
+  const uint64_t w1 = min(w0 + kZeroWords, h_words + d_words);
+  if (w0 < h_words) zero_words(r.H, w0, min(w1, h_words));
+  if (w1 > h_words) zero_words(reinterpret_cast<uint32_t*>(r.desc), max(w0, h_words) - h_words, w1 - h_words);
 }
 
 template <typename KeyT, int MODE>
@@ -146,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
   extern __shared__ __align__(16) uint8_t dyn[];
   __shared__ uint64_t s_best[kThreads / 32];
   __shared__ uint32_t s_prefix[kThreads / 32];
-  __shared__ uint32_t s_base, s_slot, s_ph, s_item, s_cmd, s_exit;
+  __shared__ uint32_t s_base, s_slot, s_ph, s_item, s_tag, s_cmd, s_exit;
   __shared__ __align__(16) Req s_req;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   uint64_t idle_since = 0;  // thread 0 only
@@ -169,14 +167,11 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
       bool done = true;
       if (tid < len) {
         const uint32_t slot = wb + tid;
-        const uint32_t ph = ld_acquire_u32(&L.st[slot].phase);
+        const unsigned long long w = ld_volatile_u64(&L.st[slot].word);
+        const uint32_t ph = word_phase(w);
         done = (ph == PH_DONE);
-        if (ph >= PH_ZERO && ph <= PH_EXPAND) {
-          const uint64_t seq = L.served ? ld_volatile_u64(&L.st[slot].seq) : (uint64_t)slot;
-          const uint64_t c = ld_volatile_u64(&L.st[slot].claim[ph - 1]);
-          const uint32_t cnt = ld_volatile_u32(&L.reqs[slot].count[ph - 1]);
-          if ((uint32_t)c < cnt && (uint32_t)(c >> 32) == (uint32_t)seq) key = (seq << 8) | tid;
-        }
+        if (ph >= PH_ZERO && ph <= PH_EXPAND && word_next(w) < ld_volatile_u32(&L.reqs[slot].count[ph - 1]))
+          key = ((uint64_t)word_seq(w) << 8) | tid;
       }
       const uint32_t notdone = __ballot_sync(0xffffffffu, !done);
 #pragma unroll
@@ -203,24 +198,24 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
         }
         if (best != ~0ull) {
           const uint32_t slot = wb + (uint32_t)(best & 0xffu);
-          const uint32_t ph = ld_acquire_u32(&L.st[slot].phase);
+          // the returned word says what was claimed (see State)
+          const unsigned long long old = atomicAdd(&L.st[slot].word, 1ull);
+          const uint32_t ph = word_phase(old), item = word_next(old);
           s_cmd = CMD_RETRY;
-          if (ph >= PH_ZERO && ph <= PH_EXPAND) {
-            const uint32_t item = claim_item(&L.st[slot], ph, ld_volatile_u32(&L.reqs[slot].count[ph - 1]),
-                                             best >> 8, L.served != 0);
-            if (item != ~0u) {
-              s_slot = slot;
-              s_ph = ph;
-              s_item = item;
-              s_cmd = CMD_WORK;
-            }
+          if (ph >= PH_ZERO && ph <= PH_EXPAND && item < ld_volatile_u32(&L.reqs[slot].count[ph - 1])) {
+            __threadfence();  // acquire: see every write of the request's earlier phases
+            s_slot = slot;
+            s_ph = ph;
+            s_item = item;
+            s_tag = word_seq(old);
+            s_cmd = CMD_WORK;
+            L.ctl->last_work = globaltimer();
           }
         }
       }
       __syncthreads();
       if (s_cmd != CMD_SLEEP || L.served) break;  // served mode: the ring is one window
     }
-
     const uint32_t cmd = s_cmd;  // thread 0 writes it again only after the next loop-top barrier
 
     // ---- nothing to do: wait (bounded), or leave
@@ -228,10 +223,12 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
       if (tid == 0) {
         const uint64_t now = globaltimer();
         if (idle_since == 0) idle_since = now;
+        const uint64_t last = *(volatile unsigned long long*)&L.ctl->last_work;
         s_exit = 0;
         if (L.served && L.host->stop) {
           s_exit = 1;
-        } else if (now - idle_since > L.idle_ns) {
+        } else if (now - idle_since > L.idle_ns && (now > last ? now - last : 0) > L.idle_ns) {
+          // the whole engine, not just this CTA, has had no work for idle_ns
           if (!L.served) raise_error(L.err, ERRBIT_TIMEOUT);
           s_exit = 1;
         }
@@ -292,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
             c->seq_done = ld_volatile_u64(&st->seq) + 1;
           }
         }
-        st_release_u32(&st->phase, np);
+        atomicExch(&st->word, pack_word(s_tag, np, 0));
       }
     }
   }
@@ -334,11 +331,13 @@ void plan_request(const ReqPlanInput& in, Req* r) {
     r->item_keys = align_up(std::max<uint64_t>(32768, 8ull * U * r->replicas), 8192);
   const uint32_t n_hist = (uint32_t)((n + r->item_keys - 1) / r->item_keys);
   r->owned = (r->mode == MODE_SMEM32 && n_hist == 1) ? 1u : 0u;
-  r->count[PH_ZERO - 1] = r->owned ? 0u : (uint32_t)((U + kZeroWords - 1) / kZeroWords);
+  r->zero_H = r->owned ? 0u : 1u;
   r->count[PH_HIST - 1] = n_hist;
   const bool sort = in.out != nullptr && n > 0;
   r->count[PH_OFFS - 1] = sort ? (uint32_t)((U + kChunkBins - 1) / kChunkBins) : 0u;
   r->count[PH_EXPAND - 1] = sort ? (uint32_t)((n + kTileKeys - 1) / kTileKeys) : 0u;
+  const uint64_t zero_words = (r->zero_H ? U : 0) + 2ull * r->count[PH_OFFS - 1];
+  r->count[PH_ZERO - 1] = (uint32_t)((zero_words + kZeroWords - 1) / kZeroWords);
   r->out_aligned = (reinterpret_cast<uintptr_t>(in.out) & 15u) == 0;
   r->first_phase = PH_DONE;
   for (uint32_t p = PH_ZERO; p <= PH_EXPAND; ++p)
@@ -496,9 +495,8 @@ dialsort_status_t dialsort_batch_create(const dialsort_instance_t* inst, uint32_
   b->total = align_up(off + s, 256);
   for (uint32_t p = 0; p < count; ++p) {
     std::memset(&b->h_states[p], 0, sizeof(State));
-    b->h_states[p].phase = b->h_reqs[p].first_phase;
     b->h_states[p].seq = p;
-    for (int k = 0; k < 4; ++k) b->h_states[p].claim[k] = (unsigned long long)p << 32;
+    b->h_states[p].word = pack_word(p, b->h_reqs[p].first_phase, 0);
   }
   *out = b;
   return DIALSORT_OK;
@@ -521,7 +519,6 @@ dialsort_status_t dialsort_batch_launch(dialsort_batch_t b, void* ws, size_t ws_
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(base + b->off_states, b->h_states, sizeof(State) * b->count, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + b->off_ctl, 0, sizeof(Ctl), st);
-  if (e == cudaSuccess && b->scratch_bytes) e = cudaMemsetAsync(base + b->off_scratch, 0, b->scratch_bytes, st);
   if (e != cudaSuccess) return DIALSORT_ERR_CUDA;
   Launch L{};
   L.reqs = reinterpret_cast<const Req*>(base + b->off_reqs);

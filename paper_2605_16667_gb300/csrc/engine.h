@@ -32,26 +32,39 @@ struct Req {
   uint32_t crn;       // hist_device.cuh CrnMode
   uint32_t replicas;
   uint32_t words_per_copy;
-  uint32_t owned;     // the single histogram item stores every bin of H (no zero phase)
+  uint32_t owned;     // the single histogram item stores every bin of H (H needs no zeroing)
   uint32_t out_aligned;
   uint32_t count[4];  // items of the zero, histogram, offsets and expand phases
   uint32_t first_phase;
-  uint32_t pad;
+  uint32_t zero_H;    // the zero phase clears H[0..U) before clearing desc
 };
 
-// Mutable progress of one request (device memory).  `phase` is published last.
-// A claim word holds (low 32 bits of seq) << 32 | items handed out: in served
-// mode slots are reused, and a CTA claims with a compare-and-swap that fails
-// if the slot now holds a different request.
+// Mutable progress of one request (device memory).  One 64-bit word holds
+// the low 32 bits of the request's admission sequence number, its phase and
+// the number of items of that phase handed out:
+//     word = seq32 << 32 | phase << 24 | next          (next < 2^24)
+// A CTA claims with a plain atomicAdd(word, 1) and reads what it claimed from
+// the returned value, so every claim is self-describing: if the phase moved
+// on, or (served mode) the slot was given to a new request, between the CTA's
+// look and its add, the CTA has claimed a genuine item of the new phase or
+// request and does that one.  A claim whose phase is not a work phase, or
+// whose index is past the phase's item count, claims nothing.
 struct State {
-  unsigned long long claim[4];  // per phase: zero, histogram, offsets, expand
+  unsigned long long word;
   unsigned long long seq;       // admission order (smaller = older = served first)
   unsigned long long t_done;    // %globaltimer when the request finished
-  uint32_t phase;
   uint32_t done[4];             // items finished, per phase
   uint32_t err;                 // error bits of this request
-  uint32_t pad[2];
+  uint32_t pad[5];
 };
+
+__host__ __device__ inline unsigned long long pack_word(uint64_t seq, uint32_t phase, uint32_t next) {
+  return ((unsigned long long)(uint32_t)seq << 32) | ((unsigned long long)(phase & 0xffu) << 24) |
+         (unsigned long long)(next & 0xffffffu);
+}
+__host__ __device__ inline uint32_t word_phase(unsigned long long w) { return (uint32_t)(w >> 24) & 0xffu; }
+__host__ __device__ inline uint32_t word_next(unsigned long long w) { return (uint32_t)w & 0xffffffu; }
+__host__ __device__ inline uint32_t word_seq(unsigned long long w) { return (uint32_t)(w >> 32); }
 
 // Completion record in host-mapped memory (served mode).
 struct Completion {
@@ -70,8 +83,10 @@ struct HostCtl {
 
 // Control words in device memory.
 struct Ctl {
-  uint32_t tail;   // batched mode: every request below tail is finished
-  uint32_t pad[63];
+  uint32_t tail;                 // batched mode: every request below tail is finished
+  uint32_t pad0;
+  unsigned long long last_work;  // %globaltimer of the latest claimed item (any CTA)
+  uint32_t pad[60];
 };
 
 struct Launch {

@@ -124,7 +124,8 @@ struct dialsort_server_s {
   HostCtl* d_ctl = nullptr;
   Req* h_req_stage = nullptr;    // pinned, one per slot
   State* h_state_stage = nullptr;
-  uint32_t* h_phase_stage = nullptr;
+  unsigned long long* h_word_stage = nullptr;
+  Ctl* d_ctl_dev = nullptr;
   cudaStream_t engine_stream = nullptr, copy_stream = nullptr;
   cudaEvent_t engine_done = nullptr;
   bool engine_launched = false;
@@ -172,17 +173,18 @@ struct dialsort_server_s {
     const uint64_t seq = next_seq++;
     State& st = h_state_stage[s];
     std::memset(&st, 0, sizeof(State));
-    st.phase = PH_FREE;
     st.seq = seq;
-    for (int k = 0; k < 4; ++k) st.claim[k] = (unsigned long long)(uint32_t)seq << 32;
-    h_phase_stage[s] = r.first_phase;
-    // slot description, reset state, zeroed look-back descriptors, then the phase word last
+    st.word = pack_word(seq, PH_FREE, 0);
+    h_word_stage[s] = pack_word(seq, r.first_phase, 0);
+    // slot description, reset state (phase FREE: nothing claimable), then the
+    // state word with the first phase, last.  Only DMA: a kernel (even a
+    // memset) could not start while the engine occupies every SM; the
+    // request's zero phase clears its look-back descriptors on the device.
     cudaError_t e = cudaMemcpyAsync(&d_reqs[s], &r, sizeof(Req), cudaMemcpyHostToDevice, copy_stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(&d_states[s], &st, sizeof(State), cudaMemcpyHostToDevice, copy_stream);
-    if (e == cudaSuccess && r.desc) e = cudaMemsetAsync(r.desc, 0, 8ull * r.count[PH_OFFS - 1], copy_stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&d_states[s].phase, &h_phase_stage[s], 4, cudaMemcpyHostToDevice, copy_stream);
+      e = cudaMemcpyAsync(&d_states[s].word, &h_word_stage[s], 8, cudaMemcpyHostToDevice, copy_stream);
     if (e != cudaSuccess) {
       arena.release(block);
       fatal = DIALSORT_ERR_CUDA;
@@ -205,7 +207,7 @@ struct dialsort_server_s {
     Launch L{};
     L.reqs = d_reqs;
     L.st = d_states;
-    L.ctl = nullptr;
+    L.ctl = d_ctl_dev;
     L.comp = d_comp;
     L.host = d_ctl;
     L.err = dev->err;
@@ -294,7 +296,8 @@ void destroy_server(dialsort_server_s* s) {
   if (s->h_ctl) cudaFreeHost(s->h_ctl);
   if (s->h_req_stage) cudaFreeHost(s->h_req_stage);
   if (s->h_state_stage) cudaFreeHost(s->h_state_stage);
-  if (s->h_phase_stage) cudaFreeHost(s->h_phase_stage);
+  if (s->h_word_stage) cudaFreeHost(s->h_word_stage);
+  if (s->d_ctl_dev) cudaFree(s->d_ctl_dev);
   delete s;
 }
 
@@ -343,7 +346,8 @@ dialsort_status_t dialsort_server_create(const dialsort_server_cfg_t* cfg, dials
             cudaHostAlloc(&s->h_ctl, sizeof(HostCtl), cudaHostAllocMapped) == cudaSuccess &&
             cudaMallocHost(&s->h_req_stage, sizeof(Req) * s->slots) == cudaSuccess &&
             cudaMallocHost(&s->h_state_stage, sizeof(State) * s->slots) == cudaSuccess &&
-            cudaMallocHost(&s->h_phase_stage, sizeof(uint32_t) * s->slots) == cudaSuccess &&
+            cudaMallocHost(&s->h_word_stage, sizeof(unsigned long long) * s->slots) == cudaSuccess &&
+            cudaMalloc(&s->d_ctl_dev, sizeof(Ctl)) == cudaSuccess &&
             cudaStreamCreateWithFlags(&s->engine_stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&s->engine_done, cudaEventDisableTiming) == cudaSuccess;
@@ -352,7 +356,8 @@ dialsort_status_t dialsort_server_create(const dialsort_server_cfg_t* cfg, dials
     std::memset(s->h_ctl, 0, sizeof(HostCtl));
     ok = cudaHostGetDevicePointer((void**)&s->d_comp, s->h_comp, 0) == cudaSuccess &&
          cudaHostGetDevicePointer((void**)&s->d_ctl, s->h_ctl, 0) == cudaSuccess &&
-         cudaMemset(s->d_states, 0, sizeof(State) * s->slots) == cudaSuccess;
+         cudaMemset(s->d_states, 0, sizeof(State) * s->slots) == cudaSuccess &&
+         cudaMemset(s->d_ctl_dev, 0, sizeof(Ctl)) == cudaSuccess;
   }
   if (!ok) {
     destroy_server(s);
