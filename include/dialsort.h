@@ -63,6 +63,8 @@ typedef enum {
   DIALSORT_REGIME_CLUSTER = 3,    /* one packed sub-histogram spread over a CTA cluster's shared memory */
   DIALSORT_REGIME_GLOBAL_CRN = 4, /* warp CRN, then one L2 atomic per distinct key of the warp */
   DIALSORT_REGIME_GLOBAL = 5,     /* one L2 atomic per key run of a thread (no cross-lane merge) */
+  DIALSORT_REGIME_TWO_LEVEL = 6,  /* large U: partition keys by high bits, then count low bits in shared
+                                     memory per bucket (needs workspace; uint32 keys, 16-byte aligned) */
 } dialsort_regime_t;
 
 /* Launch choices for step 1.  Zero in any field means "pick automatically". */
@@ -95,6 +97,22 @@ dialsort_status_t dialsort_histogram_u16(const uint16_t* keys, uint64_t n, uint3
  */
 dialsort_status_t dialsort_histogram_ex(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
                                         const dialsort_hist_config_t* cfg, void* stream);
+
+/*
+ * Workspace bytes that dialsort_histogram_ws may use for (n, U, key_bytes):
+ * the scratch of the two-level regime when it can apply, else 0.
+ */
+size_t dialsort_histogram_workspace_size(uint64_t n, uint32_t U, uint32_t key_bytes);
+
+/*
+ * As dialsort_histogram_ex with a workspace (256-byte aligned device memory,
+ * not shared with concurrent calls).  With enough workspace the automatic
+ * plan uses the two-level regime for large universes (uint32 keys, 16-byte
+ * aligned, n >= 2^20); ws may be NULL (then it never does).
+ */
+dialsort_status_t dialsort_histogram_ws(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
+                                        const dialsort_hist_config_t* cfg, void* ws, size_t ws_bytes,
+                                        void* stream);
 
 /*
  * The autotuner's choice for a histogram of n keys of key_bytes over [0,U)
@@ -167,7 +185,8 @@ dialsort_status_t dialsort_reconstruct_noalloc(const uint32_t* H, uint32_t U, ui
 
 /* ---------------------------------------------------------------- both steps */
 
-/* Bytes of workspace dialsort_sort needs: H (4U bytes) plus the scan scratch. */
+/* Bytes of workspace dialsort_sort needs: H (4U bytes), the scan scratch and,
+ * for large universes, the two-level ingestion scratch. */
 size_t dialsort_sort_workspace_size(uint64_t n, uint32_t U);
 
 /*

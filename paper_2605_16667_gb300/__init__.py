@@ -25,7 +25,7 @@ __all__ = [
 
 OK, ERR_INVALID_ARG, ERR_KEY_RANGE, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_BUSY, ERR_OVERFLOW, ERR_WORKSPACE = range(9)
 
-REGIMES = {"auto": 0, "smem32": 1, "smem16": 2, "cluster": 3, "global_crn": 4, "global": 5}
+REGIMES = {"auto": 0, "smem32": 1, "smem16": 2, "cluster": 3, "global_crn": 4, "global": 5, "two_level": 6}
 REGIME_NAMES = {v: k for k, v in REGIMES.items()}
 
 _W4 = (torch.int32, torch.uint32)
@@ -86,17 +86,32 @@ def _config(config) -> ctypes.c_void_p | None:
     return c
 
 
+def histogram_workspace_size(n: int, U: int, width: int = 4) -> int:
+    return native.load().dialsort_histogram_workspace_size(n, U, width)
+
+
 def histogram(keys: torch.Tensor, U: int, H: torch.Tensor | None = None, *, config: dict | None = None,
-              stream=None) -> torch.Tensor:
-    """Eq. (1): H[k] = number of keys equal to k, for k in [0, U).  Returns H (int32 storage of uint32)."""
+              ws: torch.Tensor | None = None, use_workspace: bool = True, stream=None) -> torch.Tensor:
+    """Eq. (1): H[k] = number of keys equal to k, for k in [0, U).  Returns H (int32 storage of uint32).
+
+    With use_workspace (default) a workspace is passed, so large universes can use the two-level regime.
+    """
     _cuda(keys, "keys")
     w = _width(keys)
     if H is None:
         H = torch.empty(U, dtype=torch.int32, device=keys.device)
     _cuda(H, "H")
     cfg = _config(config)
-    st = native.load().dialsort_histogram_ex(keys.data_ptr(), w, keys.numel(), U, H.data_ptr(),
-                                             ctypes.byref(cfg) if cfg is not None else None, _stream(stream))
+    L = native.load()
+    need = histogram_workspace_size(keys.numel(), U, w) if use_workspace else 0
+    if need:
+        ws = _workspace(need, keys.device, ws)
+        st = L.dialsort_histogram_ws(keys.data_ptr(), w, keys.numel(), U, H.data_ptr(),
+                                     ctypes.byref(cfg) if cfg is not None else None, ws.data_ptr(), ws.numel(),
+                                     _stream(stream))
+    else:
+        st = L.dialsort_histogram_ex(keys.data_ptr(), w, keys.numel(), U, H.data_ptr(),
+                                     ctypes.byref(cfg) if cfg is not None else None, _stream(stream))
     _check(st, "dialsort_histogram")
     return H
 

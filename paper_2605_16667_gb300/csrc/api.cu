@@ -59,16 +59,35 @@ dialsort_status_t check_keys(const void* keys, uint32_t key_bytes, uint64_t n, u
   return DIALSORT_OK;
 }
 
+size_t hist_ws_bytes(uint64_t n, uint32_t U, uint32_t key_bytes) {
+  if (key_bytes != 4 || n < (1u << 20)) return 0;
+  return two_level_layout(n, U).total;
+}
+
 dialsort_status_t histogram_impl(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
-                                 const dialsort_hist_config_t* cfg, cudaStream_t st) {
+                                 const dialsort_hist_config_t* cfg, void* ws, size_t ws_bytes, cudaStream_t st) {
   dialsort_status_t s = check_keys(keys, key_bytes, n, U);
   if (s != DIALSORT_OK) return s;
   if (H == nullptr || !aligned(H, 16)) return DIALSORT_ERR_INVALID_ARG;
+  if (ws != nullptr && !aligned(ws, 256)) return DIALSORT_ERR_WORKSPACE;
   const DeviceInfo* dev = device_info();
   if (!dev) return DIALSORT_ERR_CUDA;
   HistPlan plan;
   s = plan_histogram(n, U, key_bytes, 0, cfg, *dev, &plan);
   if (s != DIALSORT_OK) return s;
+  // large universes: the two-level regime when it applies and the workspace holds its scratch
+  const bool forced = plan.regime == DIALSORT_REGIME_TWO_LEVEL;
+  const bool auto_large = (cfg == nullptr || cfg->regime == DIALSORT_REGIME_AUTO) &&
+                          (plan.regime == DIALSORT_REGIME_GLOBAL_CRN || plan.regime == DIALSORT_REGIME_GLOBAL);
+  if ((forced || auto_large) && two_level_fits(n, U, key_bytes, keys)) {
+    const TwoLevelLayout T = two_level_layout(n, U);
+    if (ws != nullptr && ws_bytes >= T.total)
+      return from_cuda(launch_two_level(static_cast<const uint32_t*>(keys), n, U, H, ws, T, plan.crn, *dev,
+                                        dev->err, st));
+    if (forced) return DIALSORT_ERR_WORKSPACE;
+  } else if (forced) {
+    return DIALSORT_ERR_INVALID_ARG;
+  }
   // Eq. (1) starts from H = 0: the Theta(U) initialisation
   cudaError_t e = cudaMemsetAsync(H, 0, (size_t)U * 4, st);
   if (e == cudaSuccess && n > 0) e = launch_histogram(keys, key_bytes, n, U, H, plan, dev->err, st);
@@ -91,18 +110,19 @@ dialsort_status_t reconstruct_impl(const uint32_t* H, uint32_t U, void* out, uin
 
 size_t sort_h_bytes(uint32_t U) { return align_up((size_t)U * 4, 256); }
 
+// sort workspace: H | reconstruction scratch | ingestion scratch
 dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, void* out, void* ws,
                             size_t ws_bytes, cudaStream_t st) {
   dialsort_status_t s = check_keys(keys, key_bytes, n, U);
   if (s != DIALSORT_OK) return s;
   if (n > 0 && (out == nullptr || !aligned(out, key_bytes))) return DIALSORT_ERR_INVALID_ARG;
-  if (ws == nullptr || !aligned(ws, 256) || ws_bytes < dialsort_sort_workspace_size(n, U))
-    return DIALSORT_ERR_WORKSPACE;
-  uint32_t* H = static_cast<uint32_t*>(ws);
-  s = histogram_impl(keys, key_bytes, n, U, H, nullptr, st);
+  const size_t hb = sort_h_bytes(U), rb = recon_layout(U, n).total, ib = hist_ws_bytes(n, U, key_bytes);
+  if (ws == nullptr || !aligned(ws, 256) || ws_bytes < hb + rb + ib) return DIALSORT_ERR_WORKSPACE;
+  char* base = static_cast<char*>(ws);
+  uint32_t* H = reinterpret_cast<uint32_t*>(base);
+  s = histogram_impl(keys, key_bytes, n, U, H, nullptr, ib ? base + hb + rb : nullptr, ib, st);
   if (s != DIALSORT_OK) return s;
-  const size_t hb = sort_h_bytes(U);
-  return reconstruct_impl(H, U, out, key_bytes, n, static_cast<char*>(ws) + hb, ws_bytes - hb, st);
+  return reconstruct_impl(H, U, out, key_bytes, n, base + hb, rb, st);
 }
 
 }  // namespace
@@ -110,16 +130,26 @@ dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, ui
 extern "C" {
 
 dialsort_status_t dialsort_histogram(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* stream) {
-  return histogram_impl(keys, 4, n, U, H, nullptr, as_stream(stream));
+  return histogram_impl(keys, 4, n, U, H, nullptr, nullptr, 0, as_stream(stream));
 }
 
 dialsort_status_t dialsort_histogram_u16(const uint16_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* stream) {
-  return histogram_impl(keys, 2, n, U, H, nullptr, as_stream(stream));
+  return histogram_impl(keys, 2, n, U, H, nullptr, nullptr, 0, as_stream(stream));
 }
 
 dialsort_status_t dialsort_histogram_ex(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
                                         const dialsort_hist_config_t* cfg, void* stream) {
-  return histogram_impl(keys, key_bytes, n, U, H, cfg, as_stream(stream));
+  return histogram_impl(keys, key_bytes, n, U, H, cfg, nullptr, 0, as_stream(stream));
+}
+
+size_t dialsort_histogram_workspace_size(uint64_t n, uint32_t U, uint32_t key_bytes) {
+  return hist_ws_bytes(n, U, key_bytes);
+}
+
+dialsort_status_t dialsort_histogram_ws(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
+                                        const dialsort_hist_config_t* cfg, void* ws, size_t ws_bytes,
+                                        void* stream) {
+  return histogram_impl(keys, key_bytes, n, U, H, cfg, ws, ws_bytes, as_stream(stream));
 }
 
 dialsort_status_t dialsort_plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
@@ -168,7 +198,9 @@ dialsort_status_t dialsort_read_chunk_offsets(const void* ws, uint32_t U, uint64
                                    cudaMemcpyDeviceToDevice, as_stream(stream)));
 }
 
-size_t dialsort_sort_workspace_size(uint64_t n, uint32_t U) { return sort_h_bytes(U) + recon_layout(U, n).total; }
+size_t dialsort_sort_workspace_size(uint64_t n, uint32_t U) {
+  return sort_h_bytes(U) + recon_layout(U, n).total + hist_ws_bytes(n, U, 4);
+}
 
 dialsort_status_t dialsort_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* out, void* ws,
                                 size_t ws_bytes, void* stream) {

@@ -114,7 +114,15 @@ dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uin
 
   uint32_t regime = c.regime;
   if (regime == DIALSORT_REGIME_CLUSTER) return DIALSORT_ERR_INVALID_ARG;  // not built in this library version
-  if (regime > DIALSORT_REGIME_GLOBAL) return DIALSORT_ERR_INVALID_ARG;
+  if (regime > DIALSORT_REGIME_TWO_LEVEL) return DIALSORT_ERR_INVALID_ARG;
+  if (regime == DIALSORT_REGIME_TWO_LEVEL) {  // resolved by the caller (needs workspace); fill the CRN choice
+    p.regime = regime;
+    p.crn = c.crn == 1 ? CRN_ON : c.crn == 2 ? CRN_OFF : CRN_ADAPTIVE;
+    p.threads = 256;
+    p.blocks = 0;
+    *plan = p;
+    return DIALSORT_OK;
+  }
   const uint64_t u32_words = align_up(U, 4);
   const uint64_t u16_words = align_up((U + 1ull) / 2ull, 4);
   if (regime == DIALSORT_REGIME_AUTO) {

@@ -89,57 +89,73 @@ struct Vec<uint16_t> {
 enum CrnMode : uint32_t { CRN_OFF = 0, CRN_ON = 1, CRN_ADAPTIVE = 2 };
 
 // Adaptive CRN: a warp turns match.any on only while equal keys are common.
-// The probe is cheap -- how many lanes hold the same key as their left
-// neighbour -- and feeds a moving score (fixed point, decay 1/8) that is the
-// same in every lane, so the decision is warp-uniform.  The score settles at
-// 64 x (equal neighbours per round); the CRN is used from one per round on.
+// The probe is cheap -- how many lanes hold the same first key as their left
+// neighbour, once per vector of keys -- and feeds a moving score (fixed
+// point, decay 1/8) that is the same in every lane, so the decision is
+// warp-uniform.  The score settles at 64 x (equal neighbours per probe); the
+// CRN is used from one per probe on.
 // match.any costs about 30x an atomic when all 32 keys differ, and merges
 // hot keys when they do not.
 constexpr uint32_t kCrnScoreOn = 64;
 
-// Ingest the KPV keys one lane holds.  Must be called by all 32 lanes of the
-// warp together (the CRN step is a warp collective); lanes with valid == false
-// contribute nothing.
+// Ingest the KPV keys one lane holds; bit j of vmask says whether key j is
+// real.  Must be called by all 32 lanes of the warp together (the CRN step
+// is a warp collective); a lane with vmask == 0 contributes nothing.  Runs of
+// equal keys are merged only across consecutive real keys.
 template <int KPV, int MODE>
-__device__ __forceinline__ void ingest(const uint32_t (&k)[KPV], bool valid, const Sink<MODE>& s, uint32_t U,
-                                       bool& bad, uint32_t crn_mode, uint32_t& score) {
-  // run length starting at each position (consecutive equal keys in the lane)
+__device__ __forceinline__ void ingest_masked(const uint32_t (&k)[KPV], uint32_t vmask, const Sink<MODE>& s,
+                                              uint32_t U, bool& bad, uint32_t crn_mode, uint32_t& score) {
+  // run length starting at each position (consecutive equal real keys in the lane)
   uint32_t cnt[KPV];
   uint32_t run = 1;
 #pragma unroll
   for (int j = KPV - 1; j >= 0; --j) {
-    if (j < KPV - 1) run = (k[j + 1] == k[j]) ? run + 1 : 1;
+    if (j < KPV - 1) run = ((vmask >> (j + 1)) & 1u) && k[j + 1] == k[j] ? run + 1 : 1;
     cnt[j] = run;
+  }
+  // the CRN decision is taken once per vector (warp-uniform); the adaptive
+  // probe looks at the first key of every lane
+  bool use_crn = crn_mode == CRN_ON;
+  if (crn_mode == CRN_ADAPTIVE) {
+    const bool a0 = (vmask & 1u) && k[0] < U;
+    const uint32_t m0 = __ballot_sync(0xffffffffu, a0);
+    const uint32_t left = __shfl_up_sync(0xffffffffu, k[0], 1);
+    const uint32_t eq = __ballot_sync(0xffffffffu, a0 && left == k[0]) & (m0 << 1);
+    score = score - (score >> 3) + 8u * (uint32_t)__popc(eq);
+    use_crn = score >= kCrnScoreOn;
+  }
+  if (!use_crn) {
+#pragma unroll
+    for (int j = 0; j < KPV; ++j) {
+      const bool real = (vmask >> j) & 1u;
+      const bool start = real && (j == 0 || !((vmask >> (j - 1)) & 1u) || k[j] != k[j - 1]);
+      const bool in_range = k[j] < U;
+      bad |= start && !in_range;
+      if (start && in_range) s.add(k[j], cnt[j]);
+    }
+    return;
   }
 #pragma unroll
   for (int j = 0; j < KPV; ++j) {
-    const bool start = valid && (j == 0 || k[j] != k[j - 1]);
+    const bool real = (vmask >> j) & 1u;
+    const bool start = real && (j == 0 || !((vmask >> (j - 1)) & 1u) || k[j] != k[j - 1]);
     const bool in_range = k[j] < U;
     bad |= start && !in_range;
     const bool act = start && in_range;
-    if (crn_mode == CRN_OFF) {
-      if (act) s.add(k[j], cnt[j]);
-      continue;
-    }
     const uint32_t m = __ballot_sync(0xffffffffu, act);
     if (m == 0) continue;
-    bool use_crn = true;
-    if (crn_mode == CRN_ADAPTIVE) {
-      const uint32_t left = __shfl_up_sync(0xffffffffu, k[j], 1);
-      const uint32_t eq = __ballot_sync(0xffffffffu, act && left == k[j]) & (m << 1);
-      score = score - (score >> 3) + 8u * (uint32_t)__popc(eq);
-      use_crn = score >= kCrnScoreOn;
-    }
-    if (use_crn) {
-      if (act) {
-        const uint32_t peers = __match_any_sync(m, k[j]);
-        const uint32_t total = __reduce_add_sync(peers, cnt[j]);
-        if ((peers & lanemask_lt()) == 0) s.add(k[j], total);
-      }
-    } else if (act) {
-      s.add(k[j], cnt[j]);
+    if (act) {
+      const uint32_t peers = __match_any_sync(m, k[j]);
+      const uint32_t total = __reduce_add_sync(peers, cnt[j]);
+      if ((peers & lanemask_lt()) == 0) s.add(k[j], total);
     }
   }
+}
+
+template <int KPV, int MODE>
+__device__ __forceinline__ void ingest(const uint32_t (&k)[KPV], bool valid, const Sink<MODE>& s, uint32_t U,
+                                       bool& bad, uint32_t crn_mode, uint32_t& score) {
+  ingest_masked<KPV, MODE>(k, valid ? ((1u << KPV) - 1u) : 0u, s, U, bad, crn_mode, score);
 }
 
 // Ingest keys[0..n) with the threads of a grid (or of one CTA): thread t of

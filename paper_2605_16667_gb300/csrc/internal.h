@@ -40,6 +40,21 @@ dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uin
 cudaError_t launch_histogram(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
                              const HistPlan& plan, uint32_t* err, cudaStream_t stream);
 
+// Two-level ingestion for large universes.  hist2.cu
+struct TwoLevelLayout {
+  uint32_t L = 0, B = 0;          // low bits per key; buckets = ceil(U / 2^L)
+  uint64_t num_tiles = 0, item_keys = 0, max_items = 0;
+  size_t off_low = 0, off_toff = 0, off_btot = 0, off_items = 0, off_nitems = 0, off_pbase = 0, total = 0;
+  bool p2_smem32 = true;          // pass-2 histograms in 32-bit counters (else packed 16-bit)
+  uint32_t words_per_copy = 0;
+};
+TwoLevelLayout two_level_layout(uint64_t n, uint32_t U);
+// Whether the two-level path applies (uint32 keys, 16-byte aligned, enough keys, bucket count in range).
+bool two_level_fits(uint64_t n, uint32_t U, uint32_t key_bytes, const void* keys);
+cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* ws,
+                             const TwoLevelLayout& T, uint32_t crn_mode, const DeviceInfo& dev, uint32_t* err,
+                             cudaStream_t stream);
+
 // Step 2.  reconstruct.cu
 constexpr uint32_t kChunkBins = 1024;  // bins per offset-scan chunk
 constexpr uint32_t kTileKeys = 8192;   // output keys per expansion tile

@@ -57,6 +57,8 @@ SIGNATURES = {
     "dialsort_histogram_u16": (STATUS, [P, U64, U32, P, P]),
     "dialsort_histogram_ex": (STATUS, [P, U32, U64, U32, P, P, P]),
     "dialsort_plan_histogram": (STATUS, [U64, U32, U32, U32, P]),
+    "dialsort_histogram_workspace_size": (SZ, [U64, U32, U32]),
+    "dialsort_histogram_ws": (STATUS, [P, U32, U64, U32, P, P, P, SZ, P]),
     "dialsort_reconstruct_workspace_size": (SZ, [U32, U64]),
     "dialsort_reconstruct": (STATUS, [P, U32, P, U64, P, SZ, P]),
     "dialsort_reconstruct_u16": (STATUS, [P, U32, P, U64, P, SZ, P]),

@@ -86,6 +86,47 @@ def test_all_keys_at_universe_ends(ds, key, U):
     np.testing.assert_array_equal(host(out), keys)
 
 
+# ---- two-level ingestion (large universes): partition by high bits, count low bits per bucket
+
+TWO_LEVEL_DISTS = ["uniform", "zipf", "all_equal", "sorted", "runs", "paper_skew", "zipf_perm", "reverse"]
+
+
+@pytest.mark.parametrize("U", [(1 << 17) + 3, 1 << 20, (1 << 22) - 1, (1 << 24) + 5])
+@pytest.mark.parametrize("dist", TWO_LEVEL_DISTS)
+@pytest.mark.parametrize("crn", ["adaptive", False, True])
+def test_two_level_regime(ds, U, dist, crn):
+    n = (1 << 20) + 8192 * 3 + 13  # ragged last tile
+    keys = gen.keys(n, U, dist, param=5000 if dist == "runs" else None, stream=31)
+    H = ds.histogram(dev(keys), U, config={"regime": "two_level", "crn": crn})
+    assert ds.stream_status() == ds.OK
+    np.testing.assert_array_equal(host(H), oracle.histogram(keys, U)[0])
+
+
+def test_two_level_out_of_range_and_needs_workspace(ds):
+    U = 1 << 20
+    keys = gen.keys((1 << 20) + 77, U, "uniform", stream=32)
+    keys[5] = U
+    keys[-3] = 0xFFFFFFFF
+    H = ds.histogram(dev(keys), U, config={"regime": "two_level"})
+    assert ds.stream_status() == ds.ERR_KEY_RANGE
+    np.testing.assert_array_equal(host(H), oracle.histogram(keys, U)[0])
+    with pytest.raises(ds.DialSortError) as e:  # forced without a workspace
+        ds.histogram(dev(keys[:1000]), U, config={"regime": "two_level"}, use_workspace=False)
+    assert e.value.status in (ds.ERR_WORKSPACE, ds.ERR_INVALID_ARG)
+    ds.stream_status()
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "all_equal"])
+def test_sort_uses_two_level_for_large_universe(ds, dist):
+    n, U = (1 << 22) + 5, 1 << 21
+    keys = gen.keys(n, U, dist, stream=33)
+    out, H = ds.sort(dev(keys), U, return_histogram=True)
+    assert ds.stream_status() == ds.OK
+    H_ref, _ = oracle.histogram(keys, U)
+    np.testing.assert_array_equal(host(H), H_ref)
+    np.testing.assert_array_equal(host(out), oracle.reconstruct(H_ref, U))
+
+
 # ---- packed 16-bit counters: carries out of a field are moved to H exactly
 
 @pytest.mark.parametrize("U", [64, 63, 4097])
