@@ -35,8 +35,6 @@ struct Item {
   uint32_t bucket, t0, t1, pad;
 };
 
-constexpr uint32_t kNoBucket = 0x7ffu;  // bucket field of a skipped key (buckets are < 2047)
-__device__ __forceinline__ uint32_t bucket_of(uint32_t w) { return (w >> 16) & 0x7ffu; }
 
 // shared-memory words before the staging buffer: counters, totals, scan scratch; a multiple of 4
 __host__ __device__ __forceinline__ uint32_t p1_stage_words(uint32_t B) {
@@ -49,7 +47,7 @@ __host__ __device__ __forceinline__ uint32_t p1_stage_words(uint32_t B) {
 // by the thread itself: one shared-memory add per run, not per key.  Counts go
 // to per-warp counters (red), a scan turns them into bases, and a second
 // atomic on the same counters hands each run its positions.
-__global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t* __restrict__ keys, uint64_t n,
+__global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t* __restrict__ keys, uint64_t n,
                                                                    uint32_t U, uint32_t L, uint32_t B,
                                                                    uint64_t num_tiles, uint16_t* __restrict__ low,
                                                                    uint16_t* __restrict__ toff,
@@ -76,10 +74,9 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     const uint32_t first = kP1Keys * tid;
     const uint4* src = reinterpret_cast<const uint4*>(keys + base + first);
 
-    // this thread's consecutive keys, one word each: low part (bits 0-15),
-    // bucket (bits 16-26, kNoBucket for a key that is skipped), run length - 1
-    // (bits 27-31, from this key to the end of its run of equal buckets)
-    uint32_t w[kP1Keys];
+    // this thread's consecutive keys; bit i of vm: key i is real and < U
+    uint32_t kv[kP1Keys];
+    uint32_t vm = 0;
 #pragma unroll
     for (uint32_t i = 0; i < kP1Keys / 4; ++i) {
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -90,42 +87,36 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
         if (first + 4 * i + 1 < len) v.y = keys[base + first + 4 * i + 1];
         if (first + 4 * i + 2 < len) v.z = keys[base + first + 4 * i + 2];
       }
-      const uint32_t kk[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (uint32_t j = 0; j < 4; ++j) {
-        const bool real = first + 4 * i + j < len;
-        const bool in_range = kk[j] < U;
-        bad |= real && !in_range;
-        const uint32_t b = (real && in_range) ? (kk[j] >> L) : kNoBucket;
-        w[4 * i + j] = (kk[j] & lowmask) | (b << 16);
-      }
+      kv[4 * i] = v.x;
+      kv[4 * i + 1] = v.y;
+      kv[4 * i + 2] = v.z;
+      kv[4 * i + 3] = v.w;
     }
-    // Runs pay off only when they are common (skew, sorted input, repeated
-    // keys); the warp decides together which way it ingests this tile.
-    bool has_run = false;
 #pragma unroll
-    for (uint32_t i = 1; i < kP1Keys; ++i) has_run |= bucket_of(w[i]) == bucket_of(w[i - 1]);
-    const bool runs = __popc(__ballot_sync(0xffffffffu, has_run)) >= 16;
+    for (uint32_t i = 0; i < kP1Keys; ++i) {
+      const bool real = first + i < len;
+      const bool ok = kv[i] < U;
+      bad |= real && !ok;
+      vm |= (real && ok) ? (1u << i) : 0u;
+    }
+    // Runs of one bucket pay off only when they are common (skew, sorted
+    // input, repeated keys); the warp decides together how it ingests the tile.
+    uint32_t same = 0;  // bit i: key i continues the bucket of key i - 1
+#pragma unroll
+    for (uint32_t i = 1; i < kP1Keys; ++i) same |= ((kv[i] >> L) == (kv[i - 1] >> L)) ? (1u << i) : 0u;
+    same &= vm & (vm << 1);
+    const bool runs = __popc(__ballot_sync(0xffffffffu, same != 0)) >= 16;
     uint32_t* wcnt = cnt + warp * B;
     if (runs) {
-      uint32_t run = 1;
-#pragma unroll
-      for (int i = kP1Keys - 1; i >= 0; --i) {
-        if (i < (int)kP1Keys - 1) run = (bucket_of(w[i + 1]) == bucket_of(w[i])) ? run + 1 : 1;
-        w[i] |= (run - 1) << 27;
-      }
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
-        const uint32_t b = bucket_of(w[i]);
-        const bool start = (i == 0 || b != bucket_of(w[i - 1])) && b != kNoBucket;
-        if (start) atomicAdd(wcnt + b, (w[i] >> 27) + 1);
+        if (((vm >> i) & 1u) && !((same >> i) & 1u))  // a run starts here; its length counts the ones after it
+          atomicAdd(wcnt + (kv[i] >> L), (uint32_t)__ffs(~(same >> (i + 1))));
       }
     } else {
 #pragma unroll
-      for (uint32_t i = 0; i < kP1Keys; ++i) {
-        const uint32_t b = bucket_of(w[i]);
-        if (b != kNoBucket) atomicAdd(wcnt + b, 1u);
-      }
+      for (uint32_t i = 0; i < kP1Keys; ++i)
+        if ((vm >> i) & 1u) atomicAdd(wcnt + (kv[i] >> L), 1u);
     }
     __syncthreads();
 
@@ -177,19 +168,19 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
       uint32_t pos = 0;
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
-        const uint32_t b = bucket_of(w[i]);
-        const bool start = (i == 0 || b != bucket_of(w[i - 1]));
-        if (b != kNoBucket) {
-          pos = start ? atomicAdd(wcnt + b, (w[i] >> 27) + 1) : pos + 1;
-          stage[pos] = (uint16_t)(w[i] & 0xffffu);
+        if ((vm >> i) & 1u) {
+          if (!((same >> i) & 1u)) {
+            pos = atomicAdd(wcnt + (kv[i] >> L), (uint32_t)__ffs(~(same >> (i + 1))));
+          } else {
+            ++pos;
+          }
+          stage[pos] = (uint16_t)(kv[i] & lowmask);
         }
       }
     } else {
 #pragma unroll
-      for (uint32_t i = 0; i < kP1Keys; ++i) {
-        const uint32_t b = bucket_of(w[i]);
-        if (b != kNoBucket) stage[atomicAdd(wcnt + b, 1u)] = (uint16_t)(w[i] & 0xffffu);
-      }
+      for (uint32_t i = 0; i < kP1Keys; ++i)
+        if ((vm >> i) & 1u) stage[atomicAdd(wcnt + (kv[i] >> L), 1u)] = (uint16_t)(kv[i] & lowmask);
     }
     __syncthreads();
     // write the grouped low parts: tile t owns low[t * 8192 ...]

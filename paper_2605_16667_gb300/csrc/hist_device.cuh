@@ -88,15 +88,17 @@ struct Vec<uint16_t> {
 
 enum CrnMode : uint32_t { CRN_OFF = 0, CRN_ON = 1, CRN_ADAPTIVE = 2 };
 
-// Adaptive CRN: a warp turns match.any on only while equal keys are common.
-// The probe is cheap -- how many lanes hold the same first key as their left
-// neighbour, once per vector of keys -- and feeds a moving score (fixed
-// point, decay 1/8) that is the same in every lane, so the decision is
+// Adaptive CRN: a warp turns match.any on only while most of its lanes hold
+// the same key.  The probe is cheap -- how many lanes hold the same first key
+// as their left neighbour, once per vector of keys -- and feeds a moving score
+// (fixed point, decay 1/8) that is the same in every lane, so the decision is
 // warp-uniform.  The score settles at 64 x (equal neighbours per probe); the
-// CRN is used from one per probe on.
-// match.any costs about 30x an atomic when all 32 keys differ, and merges
-// hot keys when they do not.
-constexpr uint32_t kCrnScoreOn = 64;
+// CRN is used from 16 per probe on.  Measured on this GPU, match.any costs
+// about 6 clocks per distinct key among the 32 lanes, while a shared-memory
+// atomic pays one pass per lane that hits the same address: merging wins only
+// when few distinct keys share a warp (all equal, long sorted runs), not for
+// a hot key among many (Zipf), where it was ~15x slower than plain atomics.
+constexpr uint32_t kCrnScoreOn = 64 * 16;
 
 // Ingest the KPV keys one lane holds; bit j of vmask says whether key j is
 // real.  Must be called by all 32 lanes of the warp together (the CRN step
@@ -105,14 +107,6 @@ constexpr uint32_t kCrnScoreOn = 64;
 template <int KPV, int MODE>
 __device__ __forceinline__ void ingest_masked(const uint32_t (&k)[KPV], uint32_t vmask, const Sink<MODE>& s,
                                               uint32_t U, bool& bad, uint32_t crn_mode, uint32_t& score) {
-  // run length starting at each position (consecutive equal real keys in the lane)
-  uint32_t cnt[KPV];
-  uint32_t run = 1;
-#pragma unroll
-  for (int j = KPV - 1; j >= 0; --j) {
-    if (j < KPV - 1) run = ((vmask >> (j + 1)) & 1u) && k[j + 1] == k[j] ? run + 1 : 1;
-    cnt[j] = run;
-  }
   // the CRN decision is taken once per vector (warp-uniform); the adaptive
   // probe looks at the first key of every lane
   bool use_crn = crn_mode == CRN_ON;
@@ -124,16 +118,24 @@ __device__ __forceinline__ void ingest_masked(const uint32_t (&k)[KPV], uint32_t
     score = score - (score >> 3) + 8u * (uint32_t)__popc(eq);
     use_crn = score >= kCrnScoreOn;
   }
-  if (!use_crn) {
+  if (!use_crn) {  // equal keys are rare here: one add per key
 #pragma unroll
     for (int j = 0; j < KPV; ++j) {
       const bool real = (vmask >> j) & 1u;
-      const bool start = real && (j == 0 || !((vmask >> (j - 1)) & 1u) || k[j] != k[j - 1]);
       const bool in_range = k[j] < U;
-      bad |= start && !in_range;
-      if (start && in_range) s.add(k[j], cnt[j]);
+      bad |= real && !in_range;
+      if (real && in_range) s.add(k[j], 1u);
     }
     return;
+  }
+  // CRN path: runs of equal keys within the lane first (the optional local
+  // accumulation of a CRN lane), then equal keys across the warp's lanes
+  uint32_t cnt[KPV];
+  uint32_t run = 1;
+#pragma unroll
+  for (int j = KPV - 1; j >= 0; --j) {
+    if (j < KPV - 1) run = ((vmask >> (j + 1)) & 1u) && k[j + 1] == k[j] ? run + 1 : 1;
+    cnt[j] = run;
   }
 #pragma unroll
   for (int j = 0; j < KPV; ++j) {
