@@ -104,11 +104,11 @@ __device__ void hist_item(const Req& r, uint32_t item, uint32_t* sh, uint32_t* e
   const uint64_t begin = (uint64_t)item * r.item_keys;
   const uint64_t end = min(begin + r.item_keys, r.n);
   const uint32_t warp = threadIdx.x >> 5;
-  if (MODE != MODE_GLOBAL) {
-    zero_smem(sh, r.replicas * r.words_per_copy);
-    __syncthreads();
-  }
-  const Sink<MODE> s{sh + (warp % r.replicas) * r.words_per_copy, r.H, r.U};
+  // the global sink keeps bins [0, S) in shared memory (hot keys), the rest in L2
+  const uint32_t S = MODE == MODE_GLOBAL ? min(r.words_per_copy, r.U) : 0u;
+  zero_smem(sh, r.replicas * r.words_per_copy);
+  __syncthreads();
+  const Sink<MODE> s{sh + (warp % r.replicas) * r.words_per_copy, r.H, r.U, S};
   bool bad = false;
   ingest_span<KeyT, MODE>(static_cast<const KeyT*>(r.keys) + begin, end - begin, r.U, s, warp * 32u, blockDim.x,
                           true, r.crn, bad);
@@ -116,10 +116,9 @@ __device__ void hist_item(const Req& r, uint32_t item, uint32_t* sh, uint32_t* e
     raise_error(err, ERRBIT_KEY_RANGE);
     atomicOr(&st->err, ERRBIT_KEY_RANGE);
   }
-  if (MODE != MODE_GLOBAL) {
-    __syncthreads();
-    flush_smem<MODE>(sh, r.replicas, r.words_per_copy, r.U, r.H, r.owned != 0);
-  }
+  __syncthreads();
+  flush_smem<MODE>(sh, r.replicas, r.words_per_copy, MODE == MODE_GLOBAL ? S : r.U, r.H,
+                   MODE != MODE_GLOBAL && r.owned != 0);
 }
 
 __device__ void run_hist(const Req& r, uint32_t item, uint32_t* sh, uint32_t* err, State* st) {
@@ -322,7 +321,7 @@ void plan_request(const ReqPlanInput& in, Req* r) {
     r->replicas = 1;
   } else {
     r->mode = MODE_GLOBAL;
-    r->words_per_copy = 0;
+    r->words_per_copy = (uint32_t)std::min<uint64_t>(align_up(U, 4), kHistSmem / 4);  // shared hot prefix
     r->replicas = 1;
   }
   if (r->mode == MODE_GLOBAL)

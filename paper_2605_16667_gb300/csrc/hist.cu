@@ -33,19 +33,17 @@ __global__ void __launch_bounds__(1024) hist_kernel(const KeyT* __restrict__ key
                                                     uint32_t words_per_copy, uint32_t crn_mode) {
   extern __shared__ __align__(16) uint32_t sh[];
   const uint32_t warp = threadIdx.x >> 5;
-  if (MODE != MODE_GLOBAL) {
-    zero_smem(sh, replicas * words_per_copy);
-    __syncthreads();
-  }
-  const Sink<MODE> s{sh + (warp % replicas) * words_per_copy, H, U};
+  // the global sink keeps bins [0, S) in shared memory (S = words_per_copy, capped at U)
+  const uint32_t S = MODE == MODE_GLOBAL ? min(words_per_copy, U) : 0u;
+  zero_smem(sh, replicas * words_per_copy);
+  __syncthreads();
+  const Sink<MODE> s{sh + (warp % replicas) * words_per_copy, H, U, S};
   bool bad = false;
   ingest_span<KeyT, MODE>(keys, n, U, s, (uint64_t)blockIdx.x * blockDim.x + warp * 32u,
                           (uint64_t)gridDim.x * blockDim.x, blockIdx.x == gridDim.x - 1, crn_mode, bad);
   if (bad) raise_error(err, ERRBIT_KEY_RANGE);
-  if (MODE != MODE_GLOBAL) {
-    __syncthreads();
-    flush_smem<MODE>(sh, replicas, words_per_copy, U, H, false);
-  }
+  __syncthreads();
+  flush_smem<MODE>(sh, replicas, words_per_copy, MODE == MODE_GLOBAL ? S : U, H, false);
 }
 
 // ---------------------------------------------------------------- host side
@@ -102,6 +100,8 @@ cudaError_t launch_histogram(const void* keys, uint32_t key_bytes, uint64_t n, u
 //     is small next to n.
 //   * the global regime pays one L2 atomic per key run (per distinct key of a
 //     warp with the CRN on); with H resident in L2 it needs no merge at all.
+constexpr uint32_t kGlobalHotBins = 8192;  // 32 KB: two 1024-thread CTAs per SM still fit
+
 dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
                                  const dialsort_hist_config_t* cfg, const DeviceInfo& dev, HistPlan* plan) {
   dialsort_hist_config_t c = cfg ? *cfg : dialsort_hist_config_t{0, 0, 0, 0, 0, 0};
@@ -171,9 +171,10 @@ dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uin
     if (blocks > max_blocks) blocks = (uint32_t)max_blocks;
     p.blocks = c.blocks ? c.blocks : blocks;
   } else {
+    // the low bins in shared memory (hot keys), the rest in L2
     p.replicas = 1;
-    p.words_per_copy = 0;
-    p.smem_bytes = 0;
+    p.words_per_copy = (uint32_t)std::min<uint64_t>(align_up(U, 4), kGlobalHotBins);
+    p.smem_bytes = (size_t)p.words_per_copy * 4;
     uint64_t vec_per_thread = 16;  // aim for a handful of loop trips per thread
     uint64_t want = (n / (16 / key_bytes) + (uint64_t)p.threads * vec_per_thread - 1) / ((uint64_t)p.threads * vec_per_thread);
     uint64_t blocks = std::min<uint64_t>((uint64_t)sms * (2048u / p.threads), std::max<uint64_t>(1, want));

@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kP2Threads, 2) bucket_kernel(const uint16_t* _
   const uint64_t b_lo = (uint64_t)it.bucket << L;
   const uint32_t Ub = (uint32_t)(((uint64_t)U - b_lo) < (1ull << L) ? ((uint64_t)U - b_lo) : (1ull << L));
   zero_smem(sh, words_per_copy);
-  const Sink<MODE> s{sh, H + b_lo, Ub};
+  const Sink<MODE> s{sh, H + b_lo, Ub, 0u};
   bool bad = false;
   uint32_t score = 0;
   const uint4* low4 = reinterpret_cast<const uint4*>(low);

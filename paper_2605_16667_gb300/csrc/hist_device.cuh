@@ -17,6 +17,7 @@ struct Sink<MODE_SMEM32> {
   uint32_t* sh;
   uint32_t* H;
   uint32_t U;
+  uint32_t S;  // unused here
   __device__ __forceinline__ void add(uint32_t key, uint32_t c) const { atomicAdd(sh + key, c); }
 };
 
@@ -37,6 +38,7 @@ struct Sink<MODE_SMEM16> {
   uint32_t* sh;
   uint32_t* H;
   uint32_t U;
+  uint32_t S;  // unused here
   __device__ __forceinline__ void add(uint32_t key, uint32_t c) const {
     const uint32_t hi_bin = key & 1u;
     const uint32_t delta = hi_bin ? (c << 16) : c;
@@ -52,11 +54,21 @@ struct Sink<MODE_SMEM16> {
 };
 
 template <>
+// Adds go straight to the L2-resident H, except for the low bins [0, S),
+// which are counted in shared memory and merged at the end: when a few keys
+// are hot they are usually the small ones (Zipf), and a hot key at one L2
+// address serialises every add to it.
 struct Sink<MODE_GLOBAL> {
   uint32_t* sh;
   uint32_t* H;
   uint32_t U;
-  __device__ __forceinline__ void add(uint32_t key, uint32_t c) const { red_add_global(H + key, c); }
+  uint32_t S;
+  __device__ __forceinline__ void add(uint32_t key, uint32_t c) const {
+    if (key < S)
+      atomicAdd(sh + key, c);
+    else
+      red_add_global(H + key, c);
+  }
 };
 
 template <typename KeyT>
@@ -93,12 +105,21 @@ enum CrnMode : uint32_t { CRN_OFF = 0, CRN_ON = 1, CRN_ADAPTIVE = 2 };
 // as their left neighbour, once per vector of keys -- and feeds a moving score
 // (fixed point, decay 1/8) that is the same in every lane, so the decision is
 // warp-uniform.  The score settles at 64 x (equal neighbours per probe); the
-// CRN is used from 16 per probe on.  Measured on this GPU, match.any costs
+// CRN is used from 16 per probe on for shared-memory sinks (4 for the L2
+// sink, where a hot key serialises at one address).  Measured on this GPU, match.any costs
 // about 6 clocks per distinct key among the 32 lanes, while a shared-memory
 // atomic pays one pass per lane that hits the same address: merging wins only
 // when few distinct keys share a warp (all equal, long sorted runs), not for
 // a hot key among many (Zipf), where it was ~15x slower than plain atomics.
-constexpr uint32_t kCrnScoreOn = 64 * 16;
+template <int MODE>
+struct CrnThreshold {
+  static constexpr uint32_t value = 64 * 16;
+};
+// an L2 address takes one add at a time: merge equal keys sooner
+template <>
+struct CrnThreshold<MODE_GLOBAL> {
+  static constexpr uint32_t value = 64 * 4;
+};
 
 // Ingest the KPV keys one lane holds; bit j of vmask says whether key j is
 // real.  Must be called by all 32 lanes of the warp together (the CRN step
@@ -116,7 +137,7 @@ __device__ __forceinline__ void ingest_masked(const uint32_t (&k)[KPV], uint32_t
     const uint32_t left = __shfl_up_sync(0xffffffffu, k[0], 1);
     const uint32_t eq = __ballot_sync(0xffffffffu, a0 && left == k[0]) & (m0 << 1);
     score = score - (score >> 3) + 8u * (uint32_t)__popc(eq);
-    use_crn = score >= kCrnScoreOn;
+    use_crn = score >= CrnThreshold<MODE>::value;
   }
   if (!use_crn) {  // equal keys are rare here: one add per key
 #pragma unroll
@@ -217,7 +238,7 @@ __device__ __forceinline__ void zero_smem(uint32_t* sh, uint32_t words) {
 template <int MODE>
 __device__ __forceinline__ void flush_smem(const uint32_t* sh, uint32_t replicas, uint32_t words_per_copy,
                                            uint32_t U, uint32_t* H, bool store) {
-  if (MODE == MODE_SMEM32) {
+  if (MODE == MODE_SMEM32 || MODE == MODE_GLOBAL) {  // (the global sink: U = its shared prefix S)
     for (uint32_t b = threadIdx.x; b < U; b += blockDim.x) {
       uint32_t sum = 0;
       for (uint32_t r = 0; r < replicas; ++r) sum += sh[r * words_per_copy + b];
