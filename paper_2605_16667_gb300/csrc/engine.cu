@@ -70,6 +70,10 @@ __device__ __forceinline__ void load_req(const Req* src, Req* dst) {
   for (uint32_t i = threadIdx.x; i < sizeof(Req) / 8; i += blockDim.x) d[i] = s[i];
 }
 
+__host__ __device__ __forceinline__ uint64_t num_chunks_of(const Req& r) {
+  return ((uint64_t)r.U + kChunkBins - 1) / kChunkBins;
+}
+
 __device__ __forceinline__ uint32_t next_phase(const Req& r, uint32_t ph) {
   for (uint32_t p = ph + 1; p <= PH_EXPAND; ++p)
     if (r.count[p - 1]) return p;
@@ -92,7 +96,7 @@ __device__ void zero_words(uint32_t* p, uint64_t w0, uint64_t w1) {  // p 16-byt
 
 __device__ void zero_item(const Req& r, uint32_t item) {
   const uint64_t h_words = r.zero_H ? (uint64_t)r.U : 0;
-  const uint64_t d_words = r.desc ? 2ull * r.count[PH_OFFS - 1] : 0;
+  const uint64_t d_words = r.desc ? 2ull * r.count[PH_OFFS - 1] : 0;  // one descriptor per offsets group
   const uint64_t w0 = (uint64_t)item * kZeroWords;
   const uint64_t w1 = min(w0 + kZeroWords, h_words + d_words);
   if (w0 < h_words) zero_words(r.H, w0, min(w1, h_words));
@@ -256,15 +260,15 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
         run_hist(r, item, reinterpret_cast<uint32_t*>(dyn), L.err, st);
         break;
       case PH_OFFS:
-        offsets_chunk(r.H, r.U, r.n, r.count[PH_OFFS - 1], item, r.desc, r.O, r.first, L.err,
+        offsets_group(r.H, r.U, r.n, num_chunks_of(r), item, r.desc, r.O, r.first, L.err,
                       *reinterpret_cast<OffsetsSmem*>(dyn));
         break;
       default:
         if (r.key_bytes == 4)
-          expand_tile<uint32_t>(r.H, r.U, r.n, r.count[PH_OFFS - 1], r.O, r.first, static_cast<uint32_t*>(r.out),
+          expand_tile<uint32_t>(r.H, r.U, r.n, num_chunks_of(r), r.O, r.first, static_cast<uint32_t*>(r.out),
                                 r.out_aligned, item, *reinterpret_cast<ExpandSmem*>(dyn));
         else
-          expand_tile<uint16_t>(r.H, r.U, r.n, r.count[PH_OFFS - 1], r.O, r.first, static_cast<uint16_t*>(r.out),
+          expand_tile<uint16_t>(r.H, r.U, r.n, num_chunks_of(r), r.O, r.first, static_cast<uint16_t*>(r.out),
                                 r.out_aligned, item, *reinterpret_cast<ExpandSmem*>(dyn));
         break;
     }
@@ -333,7 +337,7 @@ void plan_request(const ReqPlanInput& in, Req* r) {
   r->zero_H = r->owned ? 0u : 1u;
   r->count[PH_HIST - 1] = n_hist;
   const bool sort = in.out != nullptr && n > 0;
-  r->count[PH_OFFS - 1] = sort ? (uint32_t)((U + kChunkBins - 1) / kChunkBins) : 0u;
+  r->count[PH_OFFS - 1] = sort ? (uint32_t)offset_groups((U + kChunkBins - 1) / kChunkBins) : 0u;
   r->count[PH_EXPAND - 1] = sort ? (uint32_t)((n + kTileKeys - 1) / kTileKeys) : 0u;
   const uint64_t zero_words = (r->zero_H ? U : 0) + 2ull * r->count[PH_OFFS - 1];
   r->count[PH_ZERO - 1] = (uint32_t)((zero_words + kZeroWords - 1) / kZeroWords);
@@ -346,22 +350,26 @@ void plan_request(const ReqPlanInput& in, Req* r) {
     }
 }
 
+// scratch of a sorting request: look-back descriptors (one per offsets group),
+// chunk offsets O[0..chunks] and the first chunk of every output tile
 size_t request_scratch_bytes(const Req& r) {
-  const uint64_t chunks = r.count[PH_OFFS - 1], tiles = r.count[PH_EXPAND - 1];
-  if (chunks == 0) return 0;
-  return align_up(8 * chunks, 256) + align_up(8 * (chunks + 1), 256) + align_up(4 * std::max<uint64_t>(tiles, 1), 256);
+  const uint64_t groups = r.count[PH_OFFS - 1], tiles = r.count[PH_EXPAND - 1];
+  if (groups == 0) return 0;
+  const uint64_t chunks = num_chunks_of(r);
+  return align_up(8 * groups, 256) + align_up(8 * (chunks + 1), 256) + align_up(4 * std::max<uint64_t>(tiles, 1), 256);
 }
 
 void place_request_scratch(Req* r, char* base) {
-  const uint64_t chunks = r->count[PH_OFFS - 1];
-  if (chunks == 0) {
+  const uint64_t groups = r->count[PH_OFFS - 1];
+  if (groups == 0) {
     r->desc = nullptr;
     r->O = nullptr;
     r->first = nullptr;
     return;
   }
+  const uint64_t chunks = num_chunks_of(*r);
   r->desc = reinterpret_cast<uint64_t*>(base);
-  base += align_up(8 * chunks, 256);
+  base += align_up(8 * groups, 256);
   r->O = reinterpret_cast<uint64_t*>(base);
   base += align_up(8 * (chunks + 1), 256);
   r->first = reinterpret_cast<uint32_t*>(base);

@@ -56,33 +56,50 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* red, T* total) {
 }
 
 struct OffsetsSmem {
-  uint64_t red[kReconThreads / 32 + 1];
-  uint64_t excl;
+  uint64_t wsum[kReconThreads / 32];  // each warp's chunk total
+  uint64_t gexcl;                     // the group's exclusive prefix
 };
 
-// Chunk c of the offset scan: its total, its exclusive prefix by decoupled
-// look-back over desc[0..c), O[c] (and O[num_chunks] for the last chunk), and
-// the first chunk of every output tile whose first key falls in the chunk's
-// run range.  The caller guarantees that every chunk below c has already been
-// handed to a running CTA (tickets taken in order), so the look-back ends.
-__device__ __forceinline__ void offsets_chunk(const uint32_t* __restrict__ H, uint32_t U, uint64_t n_cap,
-                                              uint64_t num_chunks, uint64_t c, uint64_t* desc, uint64_t* O,
-                                              uint32_t* first_chunk, uint32_t* err, OffsetsSmem& sm) {
-  const uint32_t tid = threadIdx.x;
-  uint32_t h[4];
-  load_bins4(H, c * kChunkBins + tid * 4ull, U, h);
-  const uint64_t mine = (uint64_t)h[0] + h[1] + h[2] + h[3];
-  uint64_t agg;
-  block_exclusive_sum<uint64_t>(mine, sm.red, &agg);
+// Sum of one 1024-bin chunk by one warp (lane l: bins 128 r + 4 l .. + 3).
+__device__ __forceinline__ uint64_t warp_chunk_sum(const uint32_t* __restrict__ H, uint32_t U, uint64_t c) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t sum = 0;
+#pragma unroll
+  for (uint32_t r = 0; r < kChunkBins / 128; ++r) {
+    uint32_t h[4];
+    load_bins4(H, c * kChunkBins + r * 128 + lane * 4ull, U, h);
+    sum += (uint64_t)h[0] + h[1] + h[2] + h[3];
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+  return sum;
+}
 
+// Group g of the offset scan: chunks [8 g, 8 g + 8), one per warp.  Computes
+// the group total, its exclusive prefix by decoupled look-back over
+// desc[0..g), O[c] for its chunks (and O[num_chunks] in the last group), and
+// the first chunk of every output tile whose first key falls in a chunk's run
+// range.  The caller guarantees that every group below g is already held by a
+// running CTA (groups are handed out in order), so the look-back ends.
+__device__ __forceinline__ void offsets_group(const uint32_t* __restrict__ H, uint32_t U, uint64_t n_cap,
+                                              uint64_t num_chunks, uint64_t g, uint64_t* desc, uint64_t* O,
+                                              uint32_t* first_chunk, uint32_t* err, OffsetsSmem& sm) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  constexpr uint32_t kG = kReconThreads / 32;  // chunks per group
+  const uint64_t c = g * kG + warp;
+  const uint64_t mine = c < num_chunks ? warp_chunk_sum(H, U, c) : 0;
+  if (lane == 0) sm.wsum[warp] = mine;
+  __syncthreads();
   if (tid == 0) {
+    uint64_t agg = 0;
+    for (uint32_t w = 0; w < kG; ++w) agg += sm.wsum[w];
     uint64_t excl = 0;
-    if (c == 0) {
+    if (g == 0) {
       st_release_u64(desc, kFlagInc | (agg & kValMask));
     } else {
-      st_release_u64(desc + c, kFlagAgg | (agg & kValMask));
+      st_release_u64(desc + g, kFlagAgg | (agg & kValMask));
       // look back over predecessors until one has published its inclusive prefix
-      int64_t j = (int64_t)c - 1;
+      int64_t j = (int64_t)g - 1;
       uint32_t spins = 0;
       while (j >= 0) {
         const uint64_t d = ld_acquire_u64(desc + j);
@@ -99,25 +116,34 @@ __device__ __forceinline__ void offsets_chunk(const uint32_t* __restrict__ H, ui
         if (flag == kFlagInc) break;
         --j;
       }
-      st_release_u64(desc + c, kFlagInc | ((excl + agg) & kValMask));
+      st_release_u64(desc + g, kFlagInc | ((excl + agg) & kValMask));
     }
-    sm.excl = excl;
-    O[c] = excl;
-    if (c == num_chunks - 1) {
-      O[num_chunks] = excl + agg;
-      if (excl + agg > n_cap) raise_error(err, ERRBIT_OVERFLOW);
-    }
+    sm.gexcl = excl;
   }
   __syncthreads();
-  // tiles whose first key falls inside this chunk's run range [excl, excl + agg)
-  const uint64_t lo = sm.excl;
-  const uint64_t hi = min(lo + agg, n_cap);
-  if (agg != 0 && lo < hi) {
-    const uint64_t t0 = (lo + kTileKeys - 1) / kTileKeys;
-    const uint64_t t1 = (hi - 1) / kTileKeys;
-    for (uint64_t t = t0 + tid; t <= t1; t += kReconThreads) first_chunk[t] = (uint32_t)c;
+  if (c < num_chunks) {
+    uint64_t lo = sm.gexcl;
+    for (uint32_t w = 0; w < warp; ++w) lo += sm.wsum[w];
+    if (lane == 0) {
+      O[c] = lo;
+      if (c == num_chunks - 1) {
+        O[num_chunks] = lo + mine;
+        if (lo + mine > n_cap) raise_error(err, ERRBIT_OVERFLOW);
+      }
+    }
+    // tiles whose first key falls inside this chunk's run range [lo, lo + mine)
+    const uint64_t hi = min(lo + mine, n_cap);
+    if (mine != 0 && lo < hi) {
+      const uint64_t t0 = (lo + kTileKeys - 1) / kTileKeys;
+      const uint64_t t1 = (hi - 1) / kTileKeys;
+      for (uint64_t t = t0 + lane; t <= t1; t += 32) first_chunk[t] = (uint32_t)c;
+    }
   }
   __syncthreads();  // sm is reused by the caller's next item
+}
+
+__host__ __device__ inline uint64_t offset_groups(uint64_t num_chunks) {
+  return (num_chunks + kReconThreads / 32 - 1) / (kReconThreads / 32);
 }
 
 struct ExpandSmem {
@@ -146,27 +172,73 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
   for (uint32_t i = tid; i < kTileKeys / 4; i += kReconThreads) M4[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
 
-  // mark run starts of every chunk overlapping [tile_lo, tile_hi)
-  for (uint64_t c = first_chunk[tile]; c < num_chunks; ++c) {
-    const uint64_t oc = O[c];
-    if (oc >= tile_hi) break;
-    if (O[c + 1] == oc) continue;  // empty chunk
-    uint32_t h[4];
-    const uint64_t b0 = c * kChunkBins + tid * 4ull;
-    load_bins4(H, b0, U, h);
-    uint32_t chunk_total;
-    uint32_t s = block_exclusive_sum<uint32_t>(h[0] + h[1] + h[2] + h[3], red32, &chunk_total);
+  // Mark run starts of every chunk overlapping [tile_lo, tile_hi).  A dense
+  // tile overlaps one or two chunks: the whole CTA scans each (4 bins per
+  // thread, one load each).  A sparse tile can overlap hundreds: the chunks
+  // are shared out among the warps (warp w: c0 + w, c0 + w + 8, ...), each
+  // warp scans its chunk with shuffles alone and skips an empty chunk without
+  // reading its bins.
+  const uint64_t c0 = first_chunk[tile];
+  const uint64_t num_tiles = (n_cap + kTileKeys - 1) / kTileKeys;
+  // the next tile's first chunk bounds the chunks this tile can overlap
+  const uint64_t c_last = (tile + 1 < num_tiles && tile_hi < total) ? first_chunk[tile + 1] : num_chunks - 1;
+  if (c_last - c0 <= 1) {
+    for (uint64_t c = c0; c <= c_last && c < num_chunks; ++c) {
+      const uint64_t oc = O[c];
+      if (oc >= tile_hi) break;
+      if (O[c + 1] == oc) continue;  // empty chunk
+      uint32_t h[4];
+      const uint64_t b0 = c * kChunkBins + tid * 4ull;
+      load_bins4(H, b0, U, h);
+      uint32_t chunk_total;
+      uint32_t sc = block_exclusive_sum<uint32_t>(h[0] + h[1] + h[2] + h[3], red32, &chunk_total);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (h[j] != 0) {
-        const uint64_t start = oc + s, end = start + h[j];
-        const uint32_t mark = (uint32_t)(b0 + j) + 1u;
-        if (start >= tile_lo && start < tile_hi)
-          M[start - tile_lo] = mark;
-        else if (start < tile_lo && end > tile_lo)
-          M[0] = mark;
+      for (int j = 0; j < 4; ++j) {
+        if (h[j] != 0) {
+          const uint64_t start = oc + sc, end = start + h[j];
+          const uint32_t mark = (uint32_t)(b0 + j) + 1u;
+          if (start >= tile_lo && start < tile_hi)
+            M[start - tile_lo] = mark;
+          else if (start < tile_lo && end > tile_lo)
+            M[0] = mark;
+        }
+        sc += h[j];
       }
-      s += h[j];
+    }
+  } else {
+    for (uint64_t c = c0 + warp; c < num_chunks; c += kReconThreads / 32) {
+      const uint64_t oc = O[c];
+      if (oc >= tile_hi) break;           // every later chunk starts later still
+      if (O[c + 1] == oc) continue;       // empty chunk
+      uint64_t run = oc;                  // start of the run of the next bin
+#pragma unroll 1
+      for (uint32_t r = 0; r < kChunkBins / 128; ++r) {
+        if (run >= tile_hi) break;        // the rest of this chunk lies past the tile (warp-uniform)
+        uint32_t h[4];
+        const uint64_t b0 = c * kChunkBins + r * 128 + lane * 4ull;
+        load_bins4(H, b0, U, h);
+        const uint32_t t4 = h[0] + h[1] + h[2] + h[3];
+        uint32_t x = t4;  // inclusive scan of the lanes' sums
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+          if (lane >= (uint32_t)d) x += y;
+        }
+        uint64_t start = run + (x - t4);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (h[j] != 0) {
+            const uint64_t end = start + h[j];
+            const uint32_t mark = (uint32_t)(b0 + j) + 1u;
+            if (start >= tile_lo && start < tile_hi)
+              M[start - tile_lo] = mark;
+            else if (start < tile_lo && end > tile_lo)
+              M[0] = mark;
+          }
+          start += h[j];
+        }
+        run += __shfl_sync(0xffffffffu, x, 31);
+      }
     }
   }
   __syncthreads();

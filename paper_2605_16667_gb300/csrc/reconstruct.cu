@@ -7,17 +7,19 @@
 // this file computes the starts at two granularities and keeps the fine one
 // on chip:
 //
-//   offsets kernel  one CTA per 1024-bin chunk: the chunk's total, an
-//                   exclusive scan across chunks by decoupled look-back, and,
-//                   for every 8192-key output tile that starts inside the
-//                   chunk's run range, the tile's first chunk.  Reads H once
-//                   (4U bytes); writes 16 bytes per chunk and 4 per tile.
-//   expand kernel   one CTA per output tile.  It walks the chunks that overlap
-//                   the tile, scans each chunk's bins in shared memory to get
-//                   run starts, and marks in a tile-sized buffer the slot where
-//                   each run starts (slot 0 gets the run covering the tile's
-//                   first key).  A fill-forward scan ("latest mark wins")
-//                   turns marks into keys, which go out with 128-bit stores.
+//   offsets kernel  one CTA per group of eight 1024-bin chunks (a warp per
+//                   chunk): chunk totals, an exclusive scan across groups by
+//                   decoupled look-back, each chunk's run start O[c] and, for
+//                   every 8192-key output tile that starts inside a chunk's run
+//                   range, the tile's first chunk.  Reads H once (4U bytes);
+//                   writes about 9 bytes per chunk and 4 per tile.
+//   expand kernel   one CTA per output tile.  Its warps share out the chunks
+//                   that overlap the tile, scan each chunk's bins with warp
+//                   shuffles to get run starts, and mark in a tile-sized buffer
+//                   the slot where each run starts (slot 0 gets the run
+//                   covering the tile's first key).  A fill-forward scan
+//                   ("latest mark wins") turns marks into keys, which go out
+//                   with 128-bit stores.
 //
 // No key is compared with another: searches and scans act on counts and
 // output positions only.  Load balance is by output position, so one bin with
@@ -33,10 +35,10 @@ __global__ void __launch_bounds__(kReconThreads) offsets_kernel(const uint32_t* 
                                                                 uint32_t* ticket, uint64_t* desc, uint64_t* O,
                                                                 uint32_t* first_chunk, uint32_t* err) {
   __shared__ OffsetsSmem sm;
-  __shared__ uint32_t s_c;
-  if (threadIdx.x == 0) s_c = atomicAdd(ticket, 1u);  // dynamic order: every lower chunk is already running or done
+  __shared__ uint32_t s_g;
+  if (threadIdx.x == 0) s_g = atomicAdd(ticket, 1u);  // dynamic order: every lower group is already running or done
   __syncthreads();
-  offsets_chunk(H, U, n_cap, num_chunks, s_c, desc, O, first_chunk, err, sm);
+  offsets_group(H, U, n_cap, num_chunks, s_g, desc, O, first_chunk, err, sm);
 }
 
 template <typename OutT>
@@ -59,7 +61,7 @@ ReconLayout recon_layout(uint32_t U, uint64_t n) {
   L.off_ticket = o;
   o = align_up(o + 4, 256);
   L.off_desc = o;
-  o = align_up(o + 8 * L.num_chunks, 256);
+  o = align_up(o + 8 * offset_groups(L.num_chunks), 256);
   L.clear_bytes = o;
   L.off_offsets = o;
   o = align_up(o + 8 * (L.num_chunks + 1), 256);
@@ -74,7 +76,7 @@ cudaError_t launch_offsets(const uint32_t* H, uint32_t U, uint64_t n, void* ws, 
   char* base = static_cast<char*>(ws);
   cudaError_t e = cudaMemsetAsync(base, 0, L.clear_bytes, stream);
   if (e != cudaSuccess) return e;
-  offsets_kernel<<<(unsigned)L.num_chunks, kReconThreads, 0, stream>>>(
+  offsets_kernel<<<(unsigned)offset_groups(L.num_chunks), kReconThreads, 0, stream>>>(
       H, U, n, L.num_chunks, reinterpret_cast<uint32_t*>(base + L.off_ticket),
       reinterpret_cast<uint64_t*>(base + L.off_desc), reinterpret_cast<uint64_t*>(base + L.off_offsets),
       reinterpret_cast<uint32_t*>(base + L.off_first), err);
