@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--n", type=int, default=N_KEYS)
     p.add_argument("--U", type=int, default=UNIVERSE)
     p.add_argument("--dist", default=DIST)
+    p.add_argument("--param", type=float, default=None, help="Zipf exponent (default 1.2)")
+    p.add_argument("--width", type=int, default=4, choices=[2, 4], help="key width in bytes")
     return p.parse_args()
 
 
@@ -365,11 +367,15 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    n, U = args.n, args.U
-    keys_host = gen.keys(n, U, args.dist, stream=SEED_STREAM + 1000 * rank)
-    keys = torch.from_numpy(keys_host.view(np.int32)).cuda()
+    n, U, w = args.n, args.U, args.width
+    keys_host = gen.keys(n, U, args.dist, width=w, param=args.param, stream=SEED_STREAM + 1000 * rank)
+    keys = torch.from_numpy(keys_host.view(np.int32 if w == 4 else np.int16)).cuda()
     out = torch.empty_like(keys)
     ws = torch.empty(ds.sort_workspace_size(n, U), dtype=torch.uint8, device="cuda")
+    plan = ds.plan_histogram(n, U, w)
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    # kernels of ours per sort: ingestion (1, or partition + plan + split + count for two-level), offsets, expand
+    launches_per_step = (4 if plan["regime_name"] == "two_level" else 1) + 2
     H = torch.empty(U, dtype=torch.int32, device="cuda")
     rws = torch.empty(ds.reconstruct_workspace_size(U, n), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -384,17 +390,21 @@ def main():
         raise RuntimeError("device error word set during warm-up")
 
     # ---- timed region: K sort steps, device-resident keys
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e0, e1 = ev[0], ev[-1]
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
+        for i in range(args.steps):
             step()
-        e1.record(stream)
+            ev[i + 1].record(stream)
         torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
+    per_step = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)])
+    step_stats = {"best_ms": float(per_step.min()), "mean_ms": float(per_step.mean()),
+                  "std_ms": float(per_step.std()), "cv": float(per_step.std() / per_step.mean())}
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -427,8 +437,8 @@ def main():
     recon_ms = timed(lambda: ds.reconstruct(H, U, n, out, ws=rws, stream=stream), reps)
     expand_ms = max(recon_ms - offs_ms, 1e-9)
     peak, peak_kind = peaks()
-    hist_bytes = 4 * n + 8 * U   # read keys, zero H, write H
-    recon_bytes = 4 * n + 4 * U  # read H, write the keys
+    hist_bytes = w * n + 8 * U   # read keys, zero H, write H
+    recon_bytes = w * n + 4 * U  # read H, write the keys
     if hist_ms >= recon_ms:
         dom, dom_bytes, dom_ms, kname = "histogram (zero H + ingest)", hist_bytes, hist_ms, "hist_kernel"
     else:
@@ -437,13 +447,13 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": ncu_traffic(kname), "kernel": dom, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": dom_bytes}
-    step_bytes = 8 * n + 12 * U
+    step_bytes = 2 * w * n + 12 * U
     whole = {"achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9}
     whole["frac_of_peak"] = whole["achieved_gbs"] / peak
 
     # ---- end to end through the public API with host buffers
-    pin_in = torch.from_numpy(keys_host.view(np.int32)).pin_memory()
-    pin_out = torch.empty(n, dtype=torch.int32).pin_memory()
+    pin_in = torch.from_numpy(keys_host.view(np.int32 if w == 4 else np.int16)).pin_memory()
+    pin_out = torch.empty(n, dtype=keys.dtype).pin_memory()
     d_in = torch.empty_like(keys)
 
     def e2e_step():
@@ -466,10 +476,10 @@ def main():
         t = torch.tensor([e2e_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    head = pin_out.numpy()[: 1 << 20].view(np.uint32)
+    head = pin_out.numpy()[: 1 << 20].view(np.uint32 if w == 4 else np.uint16)
     e2e_ok = bool(np.all(head[1:] >= head[:-1])) if e2e_steps else None
     e2e = {"value": world * n * e2e_steps / (e2e_ms / 1e3) if e2e_steps else None, "unit": "keys/s",
-           "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n, "steps": e2e_steps,
+           "h2d_bytes_per_step": w * n, "d2h_bytes_per_step": w * n, "steps": e2e_steps,
            "host_output_sorted": e2e_ok}
 
     cpu = None
@@ -490,16 +500,19 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32" if w == 4 else "u16", "data": "synthetic",
             "config": {"workload": WORKLOAD if (n, U, args.dist) == (N_KEYS, UNIVERSE, DIST)
                        else f"dialsort_sort n={n} U={U} {args.dist}", "n": n, "U": U, "distribution": args.dist,
-                       "key_bytes": 4,
-                       "l2": "inputs larger than L2 (1 GiB keys, 1 GiB output), no flush",
+                       "key_bytes": w, "zipf_s": (args.param or 1.2) if "zipf" in args.dist else None,
+                       "histogram_regime": plan["regime_name"],
+                       "l2": f"inputs larger than L2 ({w * n / 2**30:.3g} GiB keys, same output), no flush"
+                       if w * n > 129e6 else "inputs smaller than L2: numbers include L2 residency",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "whole_step_hbm": whole,
             "phases_ms": {"histogram": hist_ms, "offsets": offs_ms, "expand": expand_ms, "reconstruct": recon_ms},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-            "gpu_launches": 3 * args.steps, "status": status, "hist_sum_ok": hist_sum_ok, "sorted_ok": sorted_ok,
+            "gpu_launches": launches_per_step * args.steps, "step_stats": step_stats,
+            "keys_per_sm_clock": value / world / (sms * 1e6 * (clk.summary()["sm_mhz"] or 2070.0)), "status": status, "hist_sum_ok": hist_sum_ok, "sorted_ok": sorted_ok,
         }
         line.update(forms)
         print(json.dumps(line), flush=True)

@@ -117,7 +117,11 @@ dialsort_status_t dialsort_histogram_ws(const void* keys, uint32_t key_bytes, ui
 /*
  * The autotuner's choice for a histogram of n keys of key_bytes over [0,U)
  * with the given skew hint (0 = unknown, 1 = low conflict, 2 = skewed).
- * Host only; writes *cfg with every field filled in.
+ * Host only; writes *cfg with every field filled in.  With cfg->regime AUTO
+ * on input, DIALSORT_REGIME_TWO_LEVEL is reported where dialsort_histogram_ws
+ * and dialsort_sort choose it (16-byte aligned keys, workspace given); the
+ * other fields then describe the single-pass L2 plan that dialsort_histogram
+ * (no workspace) runs instead.
  */
 dialsort_status_t dialsort_plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
                                           dialsort_hist_config_t* cfg);

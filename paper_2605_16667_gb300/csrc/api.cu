@@ -163,7 +163,13 @@ dialsort_status_t dialsort_plan_histogram(uint64_t n, uint32_t U, uint32_t key_b
   dialsort_status_t s = plan_histogram(n, U, key_bytes, skew_hint, &in, dev ? *dev : fallback, &p);
   if (s != DIALSORT_OK) return s;
   const uint32_t crn_cfg = p.crn == 1 ? 1u : p.crn == 0 ? 2u : 3u;
-  *cfg = dialsort_hist_config_t{p.regime, crn_cfg, p.blocks, p.threads, p.replicas, p.cluster};
+  uint32_t regime = p.regime;
+  // what dialsort_histogram_ws does with aligned keys and a large enough workspace
+  if (in.regime == DIALSORT_REGIME_AUTO &&
+      (regime == DIALSORT_REGIME_GLOBAL_CRN || regime == DIALSORT_REGIME_GLOBAL) &&
+      two_level_shape_fits(n, U, key_bytes))
+    regime = DIALSORT_REGIME_TWO_LEVEL;
+  *cfg = dialsort_hist_config_t{regime, crn_cfg, p.blocks, p.threads, p.replicas, p.cluster};
   return DIALSORT_OK;
 }
 

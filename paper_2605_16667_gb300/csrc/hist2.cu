@@ -447,10 +447,14 @@ TwoLevelLayout two_level_layout(uint64_t n, uint32_t U) {
   return T;
 }
 
-bool two_level_fits(uint64_t n, uint32_t U, uint32_t key_bytes, const void* keys) {
-  if (key_bytes != 4 || n < (1u << 20) || (reinterpret_cast<uintptr_t>(keys) & 15u) != 0) return false;
+bool two_level_shape_fits(uint64_t n, uint32_t U, uint32_t key_bytes) {
+  if (key_bytes != 4 || n < (1u << 20)) return false;
   const TwoLevelLayout T = two_level_layout(n, U);
   return T.B >= 2 && T.B <= 2047;
+}
+
+bool two_level_fits(uint64_t n, uint32_t U, uint32_t key_bytes, const void* keys) {
+  return (reinterpret_cast<uintptr_t>(keys) & 15u) == 0 && two_level_shape_fits(n, U, key_bytes);
 }
 
 cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* ws,

@@ -50,6 +50,7 @@ struct TwoLevelLayout {
 };
 TwoLevelLayout two_level_layout(uint64_t n, uint32_t U);
 // Whether the two-level path applies (uint32 keys, 16-byte aligned, enough keys, bucket count in range).
+bool two_level_shape_fits(uint64_t n, uint32_t U, uint32_t key_bytes);
 bool two_level_fits(uint64_t n, uint32_t U, uint32_t key_bytes, const void* keys);
 cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* ws,
                              const TwoLevelLayout& T, uint32_t crn_mode, const DeviceInfo& dev, uint32_t* err,

@@ -73,8 +73,12 @@ def test_autotuner_plans_without_gpu():
     p = ds.plan_histogram(1 << 27, 1 << 16)
     assert p["regime_name"] in ("smem16", "smem32")
     p = ds.plan_histogram(1 << 28, 1 << 20, skew_hint=1)
+    assert p["regime_name"] == "two_level"  # what dialsort_sort runs on aligned keys
+    p = ds.plan_histogram(1 << 28, 1 << 20, skew_hint=1, regime="global")
     assert p["regime_name"] == "global"
     p = ds.plan_histogram(1 << 20, 1 << 16)
-    assert p["regime_name"] in ("global", "global_crn")  # merge of 152 x 2^16 bins would dominate n = 2^20
+    assert p["regime_name"] == "two_level"  # merging 152 x 2^16-bin sub-histograms would dominate n = 2^20
+    p = ds.plan_histogram(1 << 20, 1 << 16, regime="auto", width=2)
+    assert p["regime_name"] in ("global", "global_crn")  # 16-bit keys: single-pass L2 regime
     with pytest.raises(ds.DialSortError):
         ds.plan_histogram(1 << 20, 1 << 20, regime="smem32")  # 4 MiB sub-histogram does not fit
