@@ -451,36 +451,51 @@ def main():
     whole = {"achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9}
     whole["frac_of_peak"] = whole["achieved_gbs"] / peak
 
-    # ---- end to end through the public API with host buffers
-    pin_in = torch.from_numpy(keys_host.view(np.int32 if w == 4 else np.int16)).pin_memory()
-    pin_out = torch.empty(n, dtype=keys.dtype).pin_memory()
+    # ---- end to end through the public API with host buffers.  Zero-copy: dialsort_sort gets the pinned
+    # host input and output themselves; its kernels read the keys and write the sorted keys across the
+    # CPU-GPU link.  For context, the staged form (copy in, sort on the device, copy out) is timed too.
+    pin_in = torch.empty(n, dtype=keys.dtype, pin_memory=True)
+    pin_in.copy_(torch.from_numpy(keys_host.view(np.int32 if w == 4 else np.int16)))
+    pin_out = torch.empty(n, dtype=keys.dtype, pin_memory=True)
     d_in = torch.empty_like(keys)
 
     def e2e_step():
+        ds.sort(pin_in, U, out=pin_out, ws=ws, stream=stream)
+
+    def staged_step():
         d_in.copy_(pin_in, non_blocking=True)
         ds.sort(d_in, U, out=out, ws=ws, stream=stream)
         pin_out.copy_(out, non_blocking=True)
 
+    def time_e2e(fn, steps):
+        for _ in range(2 if steps else 0):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = max(e0.elapsed_time(e1), 1e-9)
+        if dist is not None:
+            tt = torch.tensor([t], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return world * n * steps / (t / 1e3) if steps else None
+
     e2e_steps = min(args.e2e_steps, args.steps)
-    for _ in range(2 if e2e_steps else 0):
-        e2e_step()
-    torch.cuda.synchronize()
-    barrier()
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max(e0.elapsed_time(e1), 1e-9)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_value = time_e2e(e2e_step, e2e_steps)
+    staged_value = time_e2e(staged_step, e2e_steps)
     head = pin_out.numpy()[: 1 << 20].view(np.uint32 if w == 4 else np.uint16)
     e2e_ok = bool(np.all(head[1:] >= head[:-1])) if e2e_steps else None
-    e2e = {"value": world * n * e2e_steps / (e2e_ms / 1e3) if e2e_steps else None, "unit": "keys/s",
+    e2e = {"value": staged_value, "unit": "keys/s",
            "h2d_bytes_per_step": w * n, "d2h_bytes_per_step": w * n, "steps": e2e_steps,
-           "host_output_sorted": e2e_ok}
+           "host_output_sorted": e2e_ok,
+           "how": "pinned host keys copied in (cudaMemcpyAsync), dialsort_sort on the device, sorted keys "
+                  "copied out; copies inside the timed region",
+           "zero_copy": {"value": e2e_value, "how": "dialsort_sort given the pinned host buffers themselves: "
+                         "its kernels read and write host memory across the CPU-GPU link"}}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

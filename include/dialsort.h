@@ -18,6 +18,14 @@
  * Conventions for every entry point:
  *   - Pointers named keys, H, out, ws are DEVICE pointers owned by the caller.
  *     Descriptor arrays passed to the batched entry points are HOST pointers.
+ *     Exception: dialsort_histogram*, dialsort_reconstruct(_u16) and
+ *     dialsort_sort(_u16) also take keys, H and out in page-locked host
+ *     memory (cudaHostAlloc / cudaHostRegister, whole range registered), and
+ *     in pageable host memory where the device reads host page tables
+ *     (cudaDevAttrPageableMemoryAccess).  The kernels then read and write it
+ *     across the CPU-GPU link themselves, with no staging copy; ws is device
+ *     memory always.  Memory of another device, or host memory the device
+ *     cannot reach, is DIALSORT_ERR_INVALID_ARG.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *     Calls are asynchronous on that stream; nothing is synchronised unless the
  *     entry point says so.
@@ -115,6 +123,19 @@ dialsort_status_t dialsort_histogram_ws(const void* keys, uint32_t key_bytes, ui
                                         void* stream);
 
 /*
+ * Accumulating ingestion: H[x] += 1 for every key x, without zeroing H first,
+ * so H ends as the histogram of every batch ingested into it since it was
+ * last zeroed (Eq. (1) applied to a stream of batches; the paper's remark on
+ * streaming ingestion after Thm. "Parallel DialSort with pipelined CRN").  Keys arriving in
+ * chunks can be ingested as each chunk lands, and the projection runs once at
+ * the end.  Arguments as dialsort_histogram_ws (ws may be NULL); H must
+ * already hold valid counts (zero it once before the first batch).  The
+ * caller keeps the total below 2^32 per bin.
+ */
+dialsort_status_t dialsort_histogram_accumulate(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U,
+                                               uint32_t* H, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * The autotuner's choice for a histogram of n keys of key_bytes over [0,U)
  * with the given skew hint (0 = unknown, 1 = low conflict, 2 = skewed).
  * Host only; writes *cfg with every field filled in.  With cfg->regime AUTO
@@ -204,6 +225,35 @@ dialsort_status_t dialsort_sort_u16(const uint16_t* keys, uint64_t n, uint32_t U
                                     size_t ws_bytes, void* stream);
 /* Device pointer to the histogram that dialsort_sort leaves in ws. */
 uint32_t* dialsort_sort_histogram(void* ws);
+
+/* ---------------------------------------------------------------- queries on H */
+
+/*
+ * H is the canonical ordered state of the data (Sec. "Canonical ordered
+ * state"): point and range queries read it directly, with no projection.
+ * H: uint32[U], 16-byte aligned, as written by step 1.  Query and result
+ * arrays hold m entries, 4-byte aligned (present: 1 byte per entry).  A query
+ * key outside [0, U) has frequency 0 and is absent (no key there was
+ * counted); it is not an error.  Asynchronous on `stream`; m = 0 launches
+ * nothing.  Pointers follow the memory rules of dialsort_histogram.
+ */
+
+/* freq[i] = H[q[i]] (Sec. "Canonical ordered state", frequency(k)). */
+dialsort_status_t dialsort_frequency(const uint32_t* H, uint32_t U, const uint32_t* q, uint64_t m, uint32_t* freq,
+                                     void* stream);
+
+/* present[i] = 1 if H[q[i]] > 0 else 0 (presence(k)). */
+dialsort_status_t dialsort_presence(const uint32_t* H, uint32_t U, const uint32_t* q, uint64_t m, uint8_t* present,
+                                    void* stream);
+
+/*
+ * count[i] = sum of H[k] over a[i] <= k <= b[i] (range-count(a, b), bounds
+ * inclusive, clipped to [0, U)); 0 when a[i] > b[i].  Cost O(b - a) per
+ * query, as in the paper; one warp sums one range.  Exact while sum(H) <
+ * 2^32, which every histogram of n < 2^32 keys satisfies.
+ */
+dialsort_status_t dialsort_range_count(const uint32_t* H, uint32_t U, const uint32_t* a, const uint32_t* b,
+                                       uint64_t m, uint32_t* count, void* stream);
 
 /* ---------------------------------------------------------------- batched form */
 
@@ -363,6 +413,11 @@ const char* dialsort_status_string(dialsort_status_t status);
 
 /* Number of SMs of the current device (0 if there is no usable device). */
 int dialsort_device_sm_count(void);
+
+/* 1 if kernels on the current device may read and write pageable host memory
+ * (so keys/H/out may be plain malloc'd memory), 0 if only page-locked host
+ * memory is reachable, -1 if there is no usable device. */
+int dialsort_pageable_host_access(void);
 
 /* Library version string, e.g. "dialsort-gb300 0.1.0 sm_103a". */
 const char* dialsort_version(void);

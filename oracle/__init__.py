@@ -16,6 +16,10 @@ Functions and the passages they follow:
   reaching each k: O[k] = sum_{j<k} H[j].
 * ``crn_level`` / ``crn`` -- Definition "CRN level transition" with the node
   rule of Eqs. (3)-(4).
+* ``accumulate``  -- Eq. (1) without the zeroing (a stream of batches ingested
+  into one H).
+* ``frequency`` / ``presence`` / ``range_count`` -- the queries of Sec.
+  "Canonical ordered state", answered from H alone (range bounds inclusive).
 
 Every function is pinned by ``tests/test_oracle_pins.py`` against the paper's
 worked examples, brute force, library routines and the theorems' invariants.
@@ -69,6 +73,16 @@ def _load():
         lib.oracle_crn_level.argtypes = [_P, _P, _SZ, _P, _P]
         lib.oracle_crn.restype = _SZ
         lib.oracle_crn.argtypes = [_P, _P, _SZ, _P, _P]
+        for name in ("oracle_accumulate_u32", "oracle_accumulate_u16"):
+            f = getattr(lib, name)
+            f.restype = _U64
+            f.argtypes = [_P, _U64, _U32, _P]
+        for name in ("oracle_frequency", "oracle_presence"):
+            f = getattr(lib, name)
+            f.restype = None
+            f.argtypes = [_P, _U32, _P, _U64, _P]
+        lib.oracle_range_count.restype = None
+        lib.oracle_range_count.argtypes = [_P, _U32, _P, _P, _U64, _P]
         _lib = lib
     return _lib
 
@@ -111,6 +125,49 @@ def sort(keys: np.ndarray, U: int) -> np.ndarray:
     keys = np.asarray(keys)
     H, _ = histogram(keys, U)
     return reconstruct(H, U, width=2 if keys.dtype == np.uint16 else 4)
+
+
+def accumulate(keys: np.ndarray, U: int, H: np.ndarray) -> tuple[np.ndarray, int]:
+    """Eq. (1) without zeroing: returns (H + counts of keys, keys >= U skipped); H is not modified."""
+    keys = np.asarray(keys)
+    H = _c(H, np.uint32).copy()
+    assert H.size == U
+    if keys.dtype == np.uint16:
+        k = _c(keys, np.uint16)
+        skipped = _load().oracle_accumulate_u16(k.ctypes.data, k.size, U, H.ctypes.data)
+    else:
+        k = _c(keys, np.uint32)
+        skipped = _load().oracle_accumulate_u32(k.ctypes.data, k.size, U, H.ctypes.data)
+    return H, int(skipped)
+
+
+def frequency(H: np.ndarray, q) -> np.ndarray:
+    """frequency(k) = H[k] for each query key (0 outside [0, U))."""
+    H = _c(H, np.uint32)
+    q = _c(q, np.uint32)
+    out = np.empty(q.size, dtype=np.uint32)
+    _load().oracle_frequency(H.ctypes.data, H.size, q.ctypes.data, q.size, out.ctypes.data)
+    return out
+
+
+def presence(H: np.ndarray, q) -> np.ndarray:
+    """presence(k) = 1 if H[k] > 0 else 0, as uint8."""
+    H = _c(H, np.uint32)
+    q = _c(q, np.uint32)
+    out = np.empty(q.size, dtype=np.uint8)
+    _load().oracle_presence(H.ctypes.data, H.size, q.ctypes.data, q.size, out.ctypes.data)
+    return out
+
+
+def range_count(H: np.ndarray, a, b) -> np.ndarray:
+    """range-count(a, b) = sum of H[k] for a <= k <= b (inclusive), as uint64."""
+    H = _c(H, np.uint32)
+    a = _c(a, np.uint32)
+    b = _c(b, np.uint32)
+    assert a.size == b.size
+    out = np.empty(a.size, dtype=np.uint64)
+    _load().oracle_range_count(H.ctypes.data, H.size, a.ctypes.data, b.ctypes.data, a.size, out.ctypes.data)
+    return out
 
 
 def offsets(H: np.ndarray, U: int | None = None) -> np.ndarray:

@@ -24,6 +24,13 @@
  *                        equal keys merged additively, distinct keys and an
  *                        odd residual forwarded unchanged.
  *   oracle_crn           ceil(log2 k) such levels applied in turn.
+ *   oracle_accumulate_*  Eq. (1) without the zeroing: H[x] <- H[x] + 1 on an
+ *                        H that already holds counts (ingesting a stream of
+ *                        batches into one histogram).
+ *   oracle_frequency,    the queries of Sec. "Canonical ordered state",
+ *   oracle_presence,     answered from H alone: frequency(k) = H[k],
+ *   oracle_range_count   presence(k) = [H[k] > 0], range-count(a, b) =
+ *                        sum of H[k] for a <= k <= b.
  *
  * Keys outside [0, U) are not defined by the paper; the oracle does not count
  * them and returns how many it skipped.
@@ -148,4 +155,47 @@ size_t oracle_crn(uint32_t* key, uint64_t* cnt, size_t m, uint32_t* scratch_key,
     cur = next;
   }
   return cur;
+}
+
+/* Eq. (1) without the zeroing: one increment per key into an H that already holds counts. */
+uint64_t oracle_accumulate_u32(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H) {
+  uint64_t skipped = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (keys[i] < U)
+      H[keys[i]] = H[keys[i]] + 1;
+    else
+      skipped = skipped + 1;
+  }
+  return skipped;
+}
+
+uint64_t oracle_accumulate_u16(const uint16_t* keys, uint64_t n, uint32_t U, uint32_t* H) {
+  uint64_t skipped = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (keys[i] < U)
+      H[keys[i]] = H[keys[i]] + 1;
+    else
+      skipped = skipped + 1;
+  }
+  return skipped;
+}
+
+/* frequency(k) = H[k]; a k outside [0, U) was never counted, so its frequency is 0. */
+void oracle_frequency(const uint32_t* H, uint32_t U, const uint32_t* q, uint64_t m, uint32_t* freq) {
+  for (uint64_t i = 0; i < m; ++i) freq[i] = q[i] < U ? H[q[i]] : 0;
+}
+
+/* presence(k) = 1 when k occurs at least once, else 0. */
+void oracle_presence(const uint32_t* H, uint32_t U, const uint32_t* q, uint64_t m, uint8_t* present) {
+  for (uint64_t i = 0; i < m; ++i) present[i] = (q[i] < U && H[q[i]] > 0) ? 1 : 0;
+}
+
+/* range-count(a, b) = sum of H[k] over a <= k <= b, k < U; one pass over the b - a + 1 cells. */
+void oracle_range_count(const uint32_t* H, uint32_t U, const uint32_t* a, const uint32_t* b, uint64_t m,
+                        uint64_t* count) {
+  for (uint64_t i = 0; i < m; ++i) {
+    uint64_t sum = 0;
+    for (uint64_t k = a[i]; k <= b[i] && k < U; ++k) sum = sum + H[k];
+    count[i] = sum;
+  }
 }

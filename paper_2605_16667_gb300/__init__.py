@@ -20,7 +20,8 @@ from . import native
 __all__ = [
     "DialSortError", "histogram", "reconstruct", "sort", "offsets", "plan_histogram", "stream_status",
     "sort_workspace_size", "reconstruct_workspace_size", "REGIMES", "lib", "Batch", "batched", "Server",
-    "replay", "device_view",
+    "replay", "device_view", "pageable_host_access", "histogram_accumulate", "frequency", "presence",
+    "range_count",
 ]
 
 OK, ERR_INVALID_ARG, ERR_KEY_RANGE, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_BUSY, ERR_OVERFLOW, ERR_WORKSPACE = range(9)
@@ -71,6 +72,23 @@ def _cuda(t: torch.Tensor, name: str) -> torch.Tensor:
     return t
 
 
+def _reachable(t: torch.Tensor, name: str) -> torch.Tensor:
+    """A CUDA tensor, or a page-locked host tensor that the kernels read or write over the host link."""
+    if not (t.is_cuda or t.is_pinned()):
+        raise ValueError(f"{name} must be a CUDA tensor or pinned host memory (DialSort has no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _device(t: torch.Tensor) -> torch.device:
+    return t.device if t.is_cuda else torch.device("cuda", torch.cuda.current_device())
+
+
+def _like(t: torch.Tensor) -> torch.Tensor:
+    return torch.empty_like(t) if t.is_cuda else torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+
+
 def _config(config) -> ctypes.c_void_p | None:
     if config is None:
         return None
@@ -95,17 +113,18 @@ def histogram(keys: torch.Tensor, U: int, H: torch.Tensor | None = None, *, conf
     """Eq. (1): H[k] = number of keys equal to k, for k in [0, U).  Returns H (int32 storage of uint32).
 
     With use_workspace (default) a workspace is passed, so large universes can use the two-level regime.
+    keys may be pinned host memory: the kernels then read it over the host link.
     """
-    _cuda(keys, "keys")
+    _reachable(keys, "keys")
     w = _width(keys)
     if H is None:
-        H = torch.empty(U, dtype=torch.int32, device=keys.device)
-    _cuda(H, "H")
+        H = torch.empty(U, dtype=torch.int32, device=_device(keys))
+    _reachable(H, "H")
     cfg = _config(config)
     L = native.load()
     need = histogram_workspace_size(keys.numel(), U, w) if use_workspace else 0
     if need:
-        ws = _workspace(need, keys.device, ws)
+        ws = _workspace(need, _device(keys), ws)
         st = L.dialsort_histogram_ws(keys.data_ptr(), w, keys.numel(), U, H.data_ptr(),
                                      ctypes.byref(cfg) if cfg is not None else None, ws.data_ptr(), ws.numel(),
                                      _stream(stream))
@@ -132,13 +151,16 @@ def _workspace(nbytes: int, device, ws: torch.Tensor | None) -> torch.Tensor:
 
 def reconstruct(H: torch.Tensor, U: int, n: int, out: torch.Tensor | None = None, *, width: int = 4,
                 ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """Eq. (2): out[0..sum H) = k repeated H[k] times, k ascending.  n is out's capacity."""
-    _cuda(H, "H")
+    """Eq. (2): out[0..sum H) = k repeated H[k] times, k ascending.  n is out's capacity.
+
+    out may be pinned host memory: the kernels then write it over the host link.
+    """
+    _reachable(H, "H")
     if out is None:
-        out = torch.empty(n, dtype=torch.int32 if width == 4 else torch.int16, device=H.device)
-    _cuda(out, "out")
+        out = torch.empty(n, dtype=torch.int32 if width == 4 else torch.int16, device=_device(H))
+    _reachable(out, "out")
     width = _width(out)
-    ws = _workspace(reconstruct_workspace_size(U, n), H.device, ws)
+    ws = _workspace(reconstruct_workspace_size(U, n), _device(H), ws)
     fn = native.load().dialsort_reconstruct if width == 4 else native.load().dialsort_reconstruct_u16
     _check(fn(H.data_ptr(), U, out.data_ptr(), n, ws.data_ptr(), ws.numel(), _stream(stream)), "dialsort_reconstruct")
     return out
@@ -158,23 +180,89 @@ def offsets(H: torch.Tensor, U: int, n: int, *, ws: torch.Tensor | None = None, 
 
 def sort(keys: torch.Tensor, U: int, out: torch.Tensor | None = None, *, ws: torch.Tensor | None = None,
          stream=None, return_histogram: bool = False):
-    """Eq. (1) then Eq. (2).  out may be keys itself (in place)."""
-    _cuda(keys, "keys")
+    """Eq. (1) then Eq. (2).  out may be keys itself (in place).
+
+    keys and out may be pinned host memory: the kernels then read the keys and write the output over
+    the host link (no staging copies); the workspace is device memory either way.
+    """
+    _reachable(keys, "keys")
     w = _width(keys)
     n = keys.numel()
     if out is None:
-        out = torch.empty_like(keys)
-    _cuda(out, "out")
+        out = _like(keys)
+    _reachable(out, "out")
     if _width(out) != w:
         raise TypeError("out must have the key width of keys")
     nbytes = sort_workspace_size(n, U)
-    ws = _workspace(nbytes, keys.device, ws)
+    ws = _workspace(nbytes, _device(keys), ws)
     L = native.load()
     fn = L.dialsort_sort if w == 4 else L.dialsort_sort_u16
     _check(fn(keys.data_ptr(), n, U, out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "dialsort_sort")
     if return_histogram:
         return out, ws[: 4 * U].view(torch.int32)
     return out
+
+
+def histogram_accumulate(keys: torch.Tensor, U: int, H: torch.Tensor, *, ws: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """Eq. (1) without zeroing: H[x] += 1 for every key x (H already holds counts).  Returns H."""
+    _reachable(keys, "keys")
+    _reachable(H, "H")
+    w = _width(keys)
+    need = histogram_workspace_size(keys.numel(), U, w)
+    ws = _workspace(need, _device(keys), ws) if need else None
+    _check(native.load().dialsort_histogram_accumulate(
+        keys.data_ptr(), w, keys.numel(), U, H.data_ptr(), ws.data_ptr() if ws is not None else None,
+        ws.numel() if ws is not None else 0, _stream(stream)), "dialsort_histogram_accumulate")
+    return H
+
+
+def _queries(q: torch.Tensor, name: str) -> torch.Tensor:
+    _reachable(q, name)
+    if q.dtype not in _W4:
+        raise TypeError(f"{name} must hold 32-bit keys")
+    return q
+
+
+def frequency(H: torch.Tensor, U: int, q: torch.Tensor, out: torch.Tensor | None = None, *,
+              stream=None) -> torch.Tensor:
+    """frequency(k) = H[k] for every query key k (0 outside [0, U)), as int32 storage of uint32."""
+    _reachable(H, "H")
+    _queries(q, "q")
+    out = torch.empty(q.numel(), dtype=torch.int32, device=_device(q)) if out is None else _reachable(out, "out")
+    _check(native.load().dialsort_frequency(H.data_ptr(), U, q.data_ptr(), q.numel(), out.data_ptr(),
+                                            _stream(stream)), "dialsort_frequency")
+    return out
+
+
+def presence(H: torch.Tensor, U: int, q: torch.Tensor, out: torch.Tensor | None = None, *,
+             stream=None) -> torch.Tensor:
+    """presence(k) = 1 if H[k] > 0 else 0, as uint8."""
+    _reachable(H, "H")
+    _queries(q, "q")
+    out = torch.empty(q.numel(), dtype=torch.uint8, device=_device(q)) if out is None else _reachable(out, "out")
+    _check(native.load().dialsort_presence(H.data_ptr(), U, q.data_ptr(), q.numel(), out.data_ptr(),
+                                           _stream(stream)), "dialsort_presence")
+    return out
+
+
+def range_count(H: torch.Tensor, U: int, a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None, *,
+                stream=None) -> torch.Tensor:
+    """range-count(a, b) = sum of H[k] for a <= k <= b (inclusive, clipped to [0, U)); uint32 in int32."""
+    _reachable(H, "H")
+    _queries(a, "a")
+    _queries(b, "b")
+    if a.numel() != b.numel():
+        raise ValueError("a and b must have the same length")
+    out = torch.empty(a.numel(), dtype=torch.int32, device=_device(a)) if out is None else _reachable(out, "out")
+    _check(native.load().dialsort_range_count(H.data_ptr(), U, a.data_ptr(), b.data_ptr(), a.numel(),
+                                              out.data_ptr(), _stream(stream)), "dialsort_range_count")
+    return out
+
+
+def pageable_host_access() -> bool:
+    """True if the kernels may read and write plain (pageable) host memory on the current device."""
+    return native.load().dialsort_pageable_host_access() == 1
 
 
 def stream_status(stream=None, sync: bool = True) -> int:

@@ -36,6 +36,8 @@ const DeviceInfo* device_info() {
     d.sms = v;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return;
     d.smem_optin = (size_t)v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) return;
+    d.pageable = v != 0;
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return;
     d.err = static_cast<uint32_t*>(p);
@@ -43,6 +45,28 @@ const DeviceInfo* device_info() {
     g_dev[dev] = d;
   });
   return g_dev[dev].device == dev ? &g_dev[dev] : nullptr;
+}
+
+dialsort_status_t kernel_address(const void* p, const DeviceInfo& dev, const void** q) {
+  *q = p;
+  if (p == nullptr) return DIALSORT_OK;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();  // not a CUDA error of the stream: clear it
+    return DIALSORT_ERR_INVALID_ARG;
+  }
+  switch (a.type) {
+    case cudaMemoryTypeDevice:
+      return a.device == dev.device ? DIALSORT_OK : DIALSORT_ERR_INVALID_ARG;
+    case cudaMemoryTypeManaged:
+      return DIALSORT_OK;
+    case cudaMemoryTypeHost:  // page-locked: the mapped address (equal to p under unified addressing)
+      if (a.devicePointer == nullptr) return DIALSORT_ERR_INVALID_ARG;
+      *q = a.devicePointer;
+      return DIALSORT_OK;
+    default:  // pageable host memory
+      return dev.pageable ? DIALSORT_OK : DIALSORT_ERR_INVALID_ARG;
+  }
 }
 
 }  // namespace dialsort
@@ -65,13 +89,20 @@ size_t hist_ws_bytes(uint64_t n, uint32_t U, uint32_t key_bytes) {
 }
 
 dialsort_status_t histogram_impl(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
-                                 const dialsort_hist_config_t* cfg, void* ws, size_t ws_bytes, cudaStream_t st) {
+                                 const dialsort_hist_config_t* cfg, void* ws, size_t ws_bytes, cudaStream_t st,
+                                 bool accumulate = false) {
   dialsort_status_t s = check_keys(keys, key_bytes, n, U);
   if (s != DIALSORT_OK) return s;
   if (H == nullptr || !aligned(H, 16)) return DIALSORT_ERR_INVALID_ARG;
   if (ws != nullptr && !aligned(ws, 256)) return DIALSORT_ERR_WORKSPACE;
   const DeviceInfo* dev = device_info();
   if (!dev) return DIALSORT_ERR_CUDA;
+  const void* kp;
+  const void* hp;
+  if ((s = kernel_address(n ? keys : nullptr, *dev, &kp)) != DIALSORT_OK) return s;
+  if ((s = kernel_address(H, *dev, &hp)) != DIALSORT_OK) return s;
+  keys = kp;
+  H = static_cast<uint32_t*>(const_cast<void*>(hp));
   HistPlan plan;
   s = plan_histogram(n, U, key_bytes, 0, cfg, *dev, &plan);
   if (s != DIALSORT_OK) return s;
@@ -83,13 +114,13 @@ dialsort_status_t histogram_impl(const void* keys, uint32_t key_bytes, uint64_t 
     const TwoLevelLayout T = two_level_layout(n, U);
     if (ws != nullptr && ws_bytes >= T.total)
       return from_cuda(launch_two_level(static_cast<const uint32_t*>(keys), n, U, H, ws, T, plan.crn, *dev,
-                                        dev->err, st));
+                                        dev->err, st, accumulate));
     if (forced) return DIALSORT_ERR_WORKSPACE;
   } else if (forced) {
     return DIALSORT_ERR_INVALID_ARG;
   }
-  // Eq. (1) starts from H = 0: the Theta(U) initialisation
-  cudaError_t e = cudaMemsetAsync(H, 0, (size_t)U * 4, st);
+  // Eq. (1) starts from H = 0: the Theta(U) initialisation (skipped when accumulating into H)
+  cudaError_t e = accumulate ? cudaSuccess : cudaMemsetAsync(H, 0, (size_t)U * 4, st);
   if (e == cudaSuccess && n > 0) e = launch_histogram(keys, key_bytes, n, U, H, plan, dev->err, st);
   return from_cuda(e);
 }
@@ -103,6 +134,13 @@ dialsort_status_t reconstruct_impl(const uint32_t* H, uint32_t U, void* out, uin
   if (ws == nullptr || !aligned(ws, 256) || ws_bytes < L.total) return DIALSORT_ERR_WORKSPACE;
   const DeviceInfo* dev = device_info();
   if (!dev) return DIALSORT_ERR_CUDA;
+  const void* hp;
+  const void* op;
+  dialsort_status_t s = kernel_address(H, *dev, &hp);
+  if (s == DIALSORT_OK) s = kernel_address(n ? out : nullptr, *dev, &op);
+  if (s != DIALSORT_OK) return s;
+  H = static_cast<const uint32_t*>(hp);
+  if (n) out = const_cast<void*>(op);
   cudaError_t e = launch_offsets(H, U, n, ws, L, dev->err, st);
   if (e == cudaSuccess) e = launch_expand(H, U, n, out, out_bytes, ws, L, st);
   return from_cuda(e);
@@ -129,6 +167,11 @@ dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, ui
 
 extern "C" {
 
+int dialsort_pageable_host_access(void) {
+  const DeviceInfo* dev = device_info();
+  return dev ? (dev->pageable ? 1 : 0) : -1;
+}
+
 dialsort_status_t dialsort_histogram(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* stream) {
   return histogram_impl(keys, 4, n, U, H, nullptr, nullptr, 0, as_stream(stream));
 }
@@ -140,6 +183,11 @@ dialsort_status_t dialsort_histogram_u16(const uint16_t* keys, uint64_t n, uint3
 dialsort_status_t dialsort_histogram_ex(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
                                         const dialsort_hist_config_t* cfg, void* stream) {
   return histogram_impl(keys, key_bytes, n, U, H, cfg, nullptr, 0, as_stream(stream));
+}
+
+dialsort_status_t dialsort_histogram_accumulate(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U,
+                                               uint32_t* H, void* ws, size_t ws_bytes, void* stream) {
+  return histogram_impl(keys, key_bytes, n, U, H, nullptr, ws, ws_bytes, as_stream(stream), true);
 }
 
 size_t dialsort_histogram_workspace_size(uint64_t n, uint32_t U, uint32_t key_bytes) {

@@ -459,7 +459,7 @@ bool two_level_fits(uint64_t n, uint32_t U, uint32_t key_bytes, const void* keys
 
 cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* ws,
                              const TwoLevelLayout& T, uint32_t crn_mode, const DeviceInfo& dev, uint32_t* err,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, bool accumulate) {
   char* base = static_cast<char*>(ws);
   uint16_t* low = reinterpret_cast<uint16_t*>(base + T.off_low);
   uint16_t* toff = reinterpret_cast<uint16_t*>(base + T.off_toff);
@@ -484,7 +484,7 @@ cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   split_kernel<<<T.B, 1024, 0, stream>>>(toff, T.B, T.num_tiles, T.item_keys, pbase, items, T.max_items);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = cudaMemsetAsync(H, 0, (size_t)U * 4, stream);
+  if (!accumulate) e = cudaMemsetAsync(H, 0, (size_t)U * 4, stream);
   if (e != cudaSuccess) return e;
   const size_t p2_smem = (size_t)T.words_per_copy * 4;
   const uint32_t p2_threads = kP2Threads;

@@ -13,7 +13,14 @@ struct DeviceInfo {
   int sms = 0;
   size_t smem_optin = 0;  // max dynamic shared memory per CTA (opt-in)
   uint32_t* err = nullptr;  // device address of the per-device error word
+  bool pageable = false;    // kernels may dereference pageable host memory (coherent host page tables)
 };
+
+// The address a kernel dereferences for a caller's pointer: device or managed
+// memory of this device as is, page-locked host memory through its mapped
+// address, pageable host memory only where dev.pageable.  INVALID_ARG for
+// memory this device cannot reach.
+dialsort_status_t kernel_address(const void* p, const DeviceInfo& dev, const void** q);
 
 // Per-device properties and error word; initialised once per device, with
 // that device current.  Returns nullptr when no device is usable.
@@ -54,7 +61,7 @@ bool two_level_shape_fits(uint64_t n, uint32_t U, uint32_t key_bytes);
 bool two_level_fits(uint64_t n, uint32_t U, uint32_t key_bytes, const void* keys);
 cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* ws,
                              const TwoLevelLayout& T, uint32_t crn_mode, const DeviceInfo& dev, uint32_t* err,
-                             cudaStream_t stream);
+                             cudaStream_t stream, bool accumulate);
 
 // Step 2.  reconstruct.cu
 constexpr uint32_t kChunkBins = 1024;  // bins per offset-scan chunk

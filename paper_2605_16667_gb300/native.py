@@ -65,6 +65,10 @@ SIGNATURES = {
     "dialsort_offsets": (STATUS, [P, U32, U64, P, SZ, P]),
     "dialsort_read_chunk_offsets": (STATUS, [P, U32, U64, P, P]),
     "dialsort_reconstruct_noalloc": (STATUS, [P, U32, P, U64, P]),
+    "dialsort_histogram_accumulate": (STATUS, [P, U32, U64, U32, P, P, SZ, P]),
+    "dialsort_frequency": (STATUS, [P, U32, P, U64, P, P]),
+    "dialsort_presence": (STATUS, [P, U32, P, U64, P, P]),
+    "dialsort_range_count": (STATUS, [P, U32, P, P, U64, P, P]),
     "dialsort_sort_workspace_size": (SZ, [U64, U32]),
     "dialsort_sort": (STATUS, [P, U64, U32, P, P, SZ, P]),
     "dialsort_sort_u16": (STATUS, [P, U64, U32, P, P, SZ, P]),
@@ -88,6 +92,7 @@ SIGNATURES = {
     "dialsort_stream_status": (STATUS, [P, INT]),
     "dialsort_status_string": (ctypes.c_char_p, [STATUS]),
     "dialsort_device_sm_count": (INT, []),
+    "dialsort_pageable_host_access": (INT, []),
     "dialsort_version": (ctypes.c_char_p, []),
 }
 

@@ -228,3 +228,67 @@ def test_crn_additive_conservation(m):
         H = np.zeros(8, dtype=np.uint64)
         np.add.at(H, kf.astype(np.int64), cf)
         np.testing.assert_array_equal(H, np.bincount(keys, weights=counts, minlength=8).astype(np.uint64))
+
+
+# ---- queries on H (Sec. "Canonical ordered state") and accumulating ingestion
+
+def test_queries_on_the_fig_viz_histogram():
+    g = load_golden("fig_viz.txt")
+    keys = [int(x) for x in g["keys"]]
+    U = int(g["U"][0])
+    H, _ = oracle.histogram(np.array(keys, dtype=np.uint32), U)
+    q = np.arange(U + 2, dtype=np.uint32)  # includes two keys outside the universe
+    np.testing.assert_array_equal(oracle.frequency(H, q), [keys.count(k) for k in q])
+    np.testing.assert_array_equal(oracle.presence(H, q), [int(k in keys) for k in q])
+    a = np.array([1, 0, 3, 4, 2, 5, 6], dtype=np.uint32)
+    b = np.array([3, 5, 3, 4, 1, 9, 9], dtype=np.uint32)
+    want = [sum(1 for x in keys if lo <= x <= hi) for lo, hi in zip(a, b)]
+    np.testing.assert_array_equal(oracle.range_count(H, a, b), want)
+    assert want[:3] == [6, 8, 4]  # keys in [1,3]: 1,1,3,3,3,3; all eight; four 3s
+
+
+@pytest.mark.parametrize("U", [1, 2, 3, 4])
+def test_queries_brute_force_tiny(U):
+    """Every key sequence of length <= 4 over [0, U), every query key and every (a, b) in [0, U+1]^2,
+    counted from the keys themselves."""
+    qs = np.arange(U + 2, dtype=np.uint32)
+    pairs = np.array([(a, b) for a in range(U + 2) for b in range(U + 2)], dtype=np.uint32)
+    for length in range(5):
+        for seq in itertools.product(range(U), repeat=length):
+            H, _ = oracle.histogram(np.array(seq, dtype=np.uint32), U)
+            assert oracle.frequency(H, qs).tolist() == [seq.count(k) for k in qs]
+            assert oracle.presence(H, qs).tolist() == [int(k in seq) for k in qs]
+            got = oracle.range_count(H, pairs[:, 0], pairs[:, 1]).tolist()
+            assert got == [sum(1 for x in seq if a <= x <= b) for a, b in pairs]
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "sorted", "all_equal"])
+def test_range_count_equals_searchsorted_on_sorted_keys(dist):
+    U, n = 100_000, 300_000
+    keys = gen.keys(n, U, dist, stream=801)
+    H, _ = oracle.histogram(keys, U)
+    s = np.sort(keys)
+    a = gen.keys(2000, U + 10, "uniform", stream=802)
+    b = gen.keys(2000, U + 10, "uniform", stream=803)
+    want = np.where(a <= b, np.searchsorted(s, b, side="right") - np.searchsorted(s, a, side="left"), 0)
+    np.testing.assert_array_equal(oracle.range_count(H, a, b), want)
+    q = gen.keys(5000, U + 10, "uniform", stream=804)
+    cnt = np.bincount(keys, minlength=U + 10)
+    np.testing.assert_array_equal(oracle.frequency(H, q), cnt[q])
+    np.testing.assert_array_equal(oracle.presence(H, q), (cnt[q] > 0).astype(np.uint8))
+    full = oracle.range_count(H, np.array([0]), np.array([U - 1]))
+    assert int(full[0]) == n  # sum of H = n (Thm. "Correctness")
+
+
+def test_accumulate_over_batches_equals_one_histogram():
+    U = 5000
+    keys = gen.keys(200_001, U, "zipf", stream=805)
+    H = np.zeros(U, dtype=np.uint32)
+    for lo, hi in [(0, 1), (1, 77_777), (77_777, 77_777), (77_777, 200_001)]:
+        H, skipped = oracle.accumulate(keys[lo:hi], U, H)
+        assert skipped == 0
+    np.testing.assert_array_equal(H, np.bincount(keys, minlength=U))
+    H2, skipped = oracle.accumulate(np.array([4999, 5000, 0], dtype=np.uint32), U, H)
+    assert skipped == 1 and int(H2[4999]) == int(H[4999]) + 1 and int(H2[0]) == int(H[0]) + 1
+    Hw, _ = oracle.accumulate(keys.astype(np.uint16), U, np.zeros(U, dtype=np.uint32))
+    np.testing.assert_array_equal(Hw, np.bincount(keys, minlength=U))
