@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
     p.add_argument("--served-seconds", type=float, default=10.0)
-    p.add_argument("--form", default="all", choices=["all", "batched", "served"],
+    p.add_argument("--form", default="all", choices=["all", "batched", "served", "radix"],
                    help="print only the batched or served form's measurement")
     # workload-size overrides, for profiling smaller cases of the same kernels
     p.add_argument("--n", type=int, default=N_KEYS)
@@ -161,8 +161,53 @@ def cpu_baseline(n_sample: int, runs_budget_s: float = 15.0):
                       f"projection, best of {len(times)} runs"}, times
 
 
+def job_throughput(ms_local: float, keys_per_rank: int, steps: int, dist=None, device=None):
+    """Whole-job keys/s over the ranks: every rank sorted keys_per_rank keys per step; the job took as
+    long as its slowest rank (max over ranks of the timed region).  Returns (keys/s, max ms)."""
+    import torch
+
+    ms = ms_local
+    world = 1
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * keys_per_rank * steps / (ms / 1e3), ms
+
+
 def _align(x, a):
     return (x + a - 1) // a * a
+
+
+def run_radix(ds, torch, stream, n: int = 1 << 28, steps: int = 20):
+    """DialSort-Radix on n full-range int32 keys: four base-256 passes plus the first digit's count.
+
+    Algorithmic bytes: the count reads 4n; each pass reads and writes 4n (36n in all).
+    """
+    import gen
+
+    peak, peak_kind = peaks()
+    keys = torch.from_numpy(gen.words(n, stream=9 * 16 + 1).astype(np.uint32).view(np.int32)).cuda()
+    out = torch.empty_like(keys)
+    ws = torch.empty(ds.lib().dialsort_radix_workspace_size(n), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ds.radix_sort(keys, out=out, ws=ws, stream=stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        ds.radix_sort(keys, out=out, ws=ws, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    ok = bool(torch.all(out[1:] >= out[:-1]).item()) and ds.stream_status() == ds.OK
+    gbs = 36 * n / (ms / 1e3) / 1e9
+    return {"workload": f"dialsort_radix_sort_i32 n={n} full-range int32 (uniform 32-bit words)",
+            "value": n / (ms / 1e3), "unit": "keys/s", "ms_per_sort": ms, "sorted_ok": ok,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_source": peak_kind, "algorithmic_bytes_per_sort": 36 * n},
+            "gpu_launches_per_sort": 5}
 
 
 def run_batched(ds, torch, stream, reps: int = 3):
@@ -353,8 +398,12 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.form != "all":
         stream = torch.cuda.current_stream()
-        res = run_batched(ds, torch, stream) if args.form == "batched" else \
-            run_served(ds, torch, seconds=args.served_seconds)
+        if args.form == "batched":
+            res = run_batched(ds, torch, stream)
+        elif args.form == "radix":
+            res = run_radix(ds, torch, stream)
+        else:
+            res = run_served(ds, torch, seconds=args.served_seconds)
         print(json.dumps({"form": args.form, **res}), flush=True)
         return 0
     dist = None
@@ -405,11 +454,7 @@ def main():
     per_step = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)])
     step_stats = {"best_ms": float(per_step.min()), "mean_ms": float(per_step.mean()),
                   "std_ms": float(per_step.std()), "cv": float(per_step.std() / per_step.mean())}
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * args.steps / (ms / 1e3)
+    value, ms = job_throughput(ms, n, args.steps, dist, torch.device("cuda", local_rank))
 
     # sanity on the last result (outside the timed region): sorted, sum(H) = n
     sorted_ok = bool(torch.all(out[1:] >= out[:-1]).item())
@@ -478,11 +523,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         t = max(e0.elapsed_time(e1), 1e-9)
-        if dist is not None:
-            tt = torch.tensor([t], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return world * n * steps / (t / 1e3) if steps else None
+        v, _ = job_throughput(t, n, steps, dist, torch.device("cuda", local_rank))
+        return v if steps else None
 
     e2e_steps = min(args.e2e_steps, args.steps)
     e2e_value = time_e2e(e2e_step, e2e_steps)
@@ -509,6 +551,8 @@ def main():
         forms["batched"] = run_batched(ds, torch, stream)
         torch.cuda.empty_cache()
         forms["served"] = run_served(ds, torch, seconds=args.served_seconds)
+        torch.cuda.empty_cache()
+        forms["radix"] = run_radix(ds, torch, stream)
         torch.cuda.empty_cache()
 
     if rank == 0:

@@ -226,6 +226,27 @@ dialsort_status_t dialsort_sort_u16(const uint16_t* keys, uint64_t n, uint32_t U
 /* Device pointer to the histogram that dialsort_sort leaves in ws. */
 uint32_t* dialsort_sort_histogram(void* ws);
 
+/* ---------------------------------------------------------------- DialSort-Radix */
+
+/*
+ * DialSort-Radix (Sec. "Full int32 range"): sorts keys of the full 32-bit
+ * range by four stable DialSort passes over base-256 digits, least
+ * significant first (each pass: Eq. (1) on the digit with U = 256, then every
+ * key placed at its digit's cursor in input order).  _i32 sorts two's
+ * complement int32 (negative keys first); _u32 sorts unsigned.
+ * keys, out: n keys, 4-byte aligned, device memory (or host memory per the
+ * rules above); out may equal keys.  ws: dialsort_radix_workspace_size(n)
+ * bytes, 256-byte aligned (n keys of ping-pong space, the digit histograms
+ * and the look-back descriptors, which are zeroed by the call).  n < 2^32.
+ * A look-back wait that gives up (it should never) records
+ * DIALSORT_ERR_TIMEOUT in the error word; no write leaves out[0..n).
+ */
+size_t dialsort_radix_workspace_size(uint64_t n);
+dialsort_status_t dialsort_radix_sort_i32(const int32_t* keys, uint64_t n, int32_t* out, void* ws, size_t ws_bytes,
+                                          void* stream);
+dialsort_status_t dialsort_radix_sort_u32(const uint32_t* keys, uint64_t n, uint32_t* out, void* ws,
+                                          size_t ws_bytes, void* stream);
+
 /* ---------------------------------------------------------------- queries on H */
 
 /*
@@ -418,6 +439,18 @@ int dialsort_device_sm_count(void);
  * (so keys/H/out may be plain malloc'd memory), 0 if only page-locked host
  * memory is reachable, -1 if there is no usable device. */
 int dialsort_pageable_host_access(void);
+
+/*
+ * Self-test of the bounded device-side waits.  which = 0: one CTA of the
+ * offset scan; which = 1: one CTA of a DialSort-Radix pass.  Each is started
+ * on a work item whose predecessor is never published, so its look-back wait
+ * runs out (about one to two seconds) and records DIALSORT_ERR_TIMEOUT in the
+ * error word; the kernel then returns and the context stays usable.  Read the
+ * result with dialsort_stream_status(stream, 1).  ws: 256-byte aligned,
+ * dialsort_selftest_workspace_size() bytes.  The paper has no counterpart.
+ */
+size_t dialsort_selftest_workspace_size(void);
+dialsort_status_t dialsort_selftest_wait_timeout(int which, void* ws, size_t ws_bytes, void* stream);
 
 /* Library version string, e.g. "dialsort-gb300 0.1.0 sm_103a". */
 const char* dialsort_version(void);

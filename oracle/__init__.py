@@ -18,6 +18,9 @@ Functions and the passages they follow:
   rule of Eqs. (3)-(4).
 * ``accumulate``  -- Eq. (1) without the zeroing (a stream of batches ingested
   into one H).
+* ``radix_sort``  -- DialSort-Radix of Sec. "Full int32 range": four stable
+  counting passes (Eq. (1) on a base-256 digit, then placement at the digit's
+  cursor), least significant digit first; int32 keys sort as signed.
 * ``frequency`` / ``presence`` / ``range_count`` -- the queries of Sec.
   "Canonical ordered state", answered from H alone (range bounds inclusive).
 
@@ -81,6 +84,8 @@ def _load():
             f = getattr(lib, name)
             f.restype = None
             f.argtypes = [_P, _U32, _P, _U64, _P]
+        lib.oracle_radix_sort.restype = None
+        lib.oracle_radix_sort.argtypes = [_P, _U64, ctypes.c_int, _P, _P]
         lib.oracle_range_count.restype = None
         lib.oracle_range_count.argtypes = [_P, _U32, _P, _P, _U64, _P]
         _lib = lib
@@ -139,6 +144,18 @@ def accumulate(keys: np.ndarray, U: int, H: np.ndarray) -> tuple[np.ndarray, int
         k = _c(keys, np.uint32)
         skipped = _load().oracle_accumulate_u32(k.ctypes.data, k.size, U, H.ctypes.data)
     return H, int(skipped)
+
+
+def radix_sort(keys: np.ndarray) -> np.ndarray:
+    """DialSort-Radix: LSD base 256, four stable counting passes; int32 keys sort as signed."""
+    keys = np.asarray(keys)
+    assert keys.dtype in (np.int32, np.uint32)
+    k = np.ascontiguousarray(keys).view(np.uint32)
+    out = np.empty(k.size, dtype=np.uint32)
+    tmp = np.empty(k.size, dtype=np.uint32)
+    _load().oracle_radix_sort(k.ctypes.data, k.size, 1 if keys.dtype == np.int32 else 0, out.ctypes.data,
+                              tmp.ctypes.data)
+    return out.view(keys.dtype)
 
 
 def frequency(H: np.ndarray, q) -> np.ndarray:

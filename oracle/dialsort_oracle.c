@@ -27,6 +27,9 @@
  *   oracle_accumulate_*  Eq. (1) without the zeroing: H[x] <- H[x] + 1 on an
  *                        H that already holds counts (ingesting a stream of
  *                        batches into one histogram).
+ *   oracle_radix_sort    DialSort-Radix (Sec. "Full int32 range"): four
+ *                        stable counting passes over the base-256 digits,
+ *                        least significant first.
  *   oracle_frequency,    the queries of Sec. "Canonical ordered state",
  *   oracle_presence,     answered from H alone: frequency(k) = H[k],
  *   oracle_range_count   presence(k) = [H[k] > 0], range-count(a, b) =
@@ -197,5 +200,42 @@ void oracle_range_count(const uint32_t* H, uint32_t U, const uint32_t* a, const 
     uint64_t sum = 0;
     for (uint64_t k = a[i]; k <= b[i] && k < U; ++k) sum = sum + H[k];
     count[i] = sum;
+  }
+}
+
+/*
+ * DialSort-Radix (Sec. "Full int32 range"): LSD radix sort in base 256.  Pass
+ * p = 0..3 looks at digit d = (x >> 8p) & 255 only: H = histogram of the digit
+ * (Eq. (1) with U = 256), the cursor of digit d starts at the sum of H below d
+ * (the cursor of the projection of Eq. (2)), and keys are placed at
+ * cursor[d]++ in their current order, so each pass is stable and after the
+ * fourth the keys are sorted.  With is_signed the keys are two's complement
+ * int32: the top digit's sign bit is flipped, putting negative keys first.
+ * out and tmp hold n keys each; out may equal keys.
+ */
+void oracle_radix_sort(const uint32_t* keys, uint64_t n, int is_signed, uint32_t* out, uint32_t* tmp) {
+  const uint32_t* src = keys;
+  for (int pass = 0; pass < 4; ++pass) {
+    uint32_t* dst = (pass % 2 == 0) ? tmp : out;
+    uint64_t H[256];
+    uint64_t cursor[256];
+    for (int d = 0; d < 256; ++d) H[d] = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      uint32_t d = (src[i] >> (8 * pass)) & 255u;
+      if (is_signed && pass == 3) d = d ^ 0x80u;
+      H[d] = H[d] + 1;
+    }
+    uint64_t c = 0;
+    for (int d = 0; d < 256; ++d) {
+      cursor[d] = c;
+      c = c + H[d];
+    }
+    for (uint64_t i = 0; i < n; ++i) {
+      uint32_t d = (src[i] >> (8 * pass)) & 255u;
+      if (is_signed && pass == 3) d = d ^ 0x80u;
+      dst[cursor[d]] = src[i];
+      cursor[d] = cursor[d] + 1;
+    }
+    src = dst;
   }
 }

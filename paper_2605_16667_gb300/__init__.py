@@ -21,7 +21,7 @@ __all__ = [
     "DialSortError", "histogram", "reconstruct", "sort", "offsets", "plan_histogram", "stream_status",
     "sort_workspace_size", "reconstruct_workspace_size", "REGIMES", "lib", "Batch", "batched", "Server",
     "replay", "device_view", "pageable_host_access", "histogram_accumulate", "frequency", "presence",
-    "range_count",
+    "range_count", "radix_sort",
 ]
 
 OK, ERR_INVALID_ARG, ERR_KEY_RANGE, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_BUSY, ERR_OVERFLOW, ERR_WORKSPACE = range(9)
@@ -215,6 +215,30 @@ def histogram_accumulate(keys: torch.Tensor, U: int, H: torch.Tensor, *, ws: tor
         keys.data_ptr(), w, keys.numel(), U, H.data_ptr(), ws.data_ptr() if ws is not None else None,
         ws.numel() if ws is not None else 0, _stream(stream)), "dialsort_histogram_accumulate")
     return H
+
+
+def radix_sort(keys: torch.Tensor, out: torch.Tensor | None = None, *, signed: bool | None = None,
+               ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """DialSort-Radix: full-range 32-bit sort by four base-256 DialSort passes.
+
+    torch.int32 keys sort as signed, torch.uint32 as unsigned (``signed`` overrides).  out may be keys.
+    """
+    _reachable(keys, "keys")
+    if keys.dtype not in _W4:
+        raise TypeError("radix_sort takes 32-bit keys")
+    if signed is None:
+        signed = keys.dtype == torch.int32
+    n = keys.numel()
+    if out is None:
+        out = _like(keys)
+    _reachable(out, "out")
+    if out.dtype not in _W4 or out.numel() < n:
+        raise ValueError("out must hold n 32-bit keys")
+    L = native.load()
+    ws = _workspace(L.dialsort_radix_workspace_size(n), _device(keys), ws)
+    fn = L.dialsort_radix_sort_i32 if signed else L.dialsort_radix_sort_u32
+    _check(fn(keys.data_ptr(), n, out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "dialsort_radix_sort")
+    return out
 
 
 def _queries(q: torch.Tensor, name: str) -> torch.Tensor:

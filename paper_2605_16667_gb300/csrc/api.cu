@@ -1,6 +1,7 @@
 // extern "C" entry points of libdialsort.so (declared in include/dialsort.h):
 // host-side argument checks, per-device state, and the launch sequences of the
 // two steps of DialSort.
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -166,6 +167,20 @@ dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, ui
 }  // namespace
 
 extern "C" {
+
+size_t dialsort_selftest_workspace_size(void) {
+  return std::max(offsets_selftest_bytes(), radix_selftest_bytes());
+}
+
+dialsort_status_t dialsort_selftest_wait_timeout(int which, void* ws, size_t ws_bytes, void* stream) {
+  if (which != 0 && which != 1) return DIALSORT_ERR_INVALID_ARG;
+  if (ws == nullptr || !aligned(ws, 256) || ws_bytes < dialsort_selftest_workspace_size())
+    return DIALSORT_ERR_WORKSPACE;
+  const DeviceInfo* dev = device_info();
+  if (!dev) return DIALSORT_ERR_CUDA;
+  const cudaStream_t st = as_stream(stream);
+  return from_cuda(which == 0 ? launch_offsets_selftest(ws, dev->err, st) : launch_radix_selftest(ws, dev->err, st));
+}
 
 int dialsort_pageable_host_access(void) {
   const DeviceInfo* dev = device_info();

@@ -6,15 +6,17 @@
 //
 // A key k splits into a bucket b = k >> L and a low part k & (2^L - 1).
 //   pass 1 (partition_kernel)  per 8192-key tile: rank every key within its
-//          bucket (shared-memory counters per warp), scan to bucket starts,
-//          write the tile's low parts grouped by bucket (uint16), the tile's
-//          bucket starts (toff[t][0..B]) and add the bucket totals up.
-//   plan   (plan_kernel)       split every non-empty bucket into parts of
-//          about item_keys keys (contiguous tile ranges) -> work items.
+//          bucket (one shared-memory atomic per key, or per run of a bucket),
+//          scan to bucket starts, write the tile's low parts grouped by bucket
+//          (uint16), the tile's bucket starts (toff[t][0..B]) and add the
+//          bucket totals up.
+//   plan   (plan_kernel, split_kernel)  split every non-empty bucket into
+//          parts of about item_keys keys (contiguous tile ranges) -> items.
 //   pass 2 (bucket_kernel)     per item: gather the bucket's segments of the
 //          item's tiles, count the low parts in a shared-memory histogram of
-//          2^L bins (Eq. (1) on the sub-universe, with the warp CRN) and add
-//          it into H[b * 2^L ...].
+//          2^L bins (Eq. (1) on the sub-universe; eight equal low parts in a
+//          chunk merge into one add, the CRN lane's local accumulation) and
+//          add it into H[b * 2^L ...].
 // H is zeroed before pass 2.  Counting is exact: pass 1 only moves keys.
 // Only equality and shifts touch keys; key < U is checked against the bound.
 #include <algorithm>
@@ -36,87 +38,112 @@ struct Item {
 };
 
 
-// shared-memory words before the staging buffer: counters, totals, scan scratch; a multiple of 4
+// Pass-1 counters: one per (bucket, warp), bucket-major with a stride of
+// kP1Warps + 1 words, so one bucket's warp counters are contiguous for the
+// scan while one warp's buckets spread over all banks for the atomics.
+constexpr uint32_t kCntStride = kP1Warps + 1;
+
+// shared-memory words before the staging buffer: counters, bucket totals, scan scratch; a multiple of 4
 __host__ __device__ __forceinline__ uint32_t p1_stage_words(uint32_t B) {
-  return (kP1Warps * B + B + 16 + 3) & ~3u;
+  return (B * kCntStride + B + 32 + 3) & ~3u;
 }
 
 // ------------------------------------------------------------------ pass 1
-// Thread tid owns keys [16 tid, 16 tid + 16) of the tile, so runs of keys with
-// the same bucket (long under skew, sorted input or repeated keys) are merged
-// by the thread itself: one shared-memory add per run, not per key.  Counts go
-// to per-warp counters (red), a scan turns them into bases, and a second
-// atomic on the same counters hands each run its positions.
+// Thread tid owns keys [16 tid, 16 tid + 16) of the tile.  Each key takes its
+// rank with one shared-memory atomic on its (bucket, warp) counter and keeps
+// it in a register; a scan turns the counters into bases, and base + rank is
+// the key's slot in the tile's bucket-grouped order.  Runs of one bucket
+// within a thread (skew, sorted input, repeated keys) take one atomic per
+// run; the warp decides together whether to look for runs.
 __global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t* __restrict__ keys, uint64_t n,
                                                                    uint32_t U, uint32_t L, uint32_t B,
                                                                    uint64_t num_tiles, uint16_t* __restrict__ low,
                                                                    uint16_t* __restrict__ toff,
-                                                                   uint32_t* __restrict__ btot, uint32_t* err,
-                                                                   uint32_t crn_mode) {
-  (void)crn_mode;
+                                                                   uint32_t* __restrict__ btot, uint32_t* err) {
   extern __shared__ __align__(16) uint32_t sm[];
-  uint32_t* cnt = sm;                          // [kP1Warps][B]: counts, then bases / cursors
-  uint32_t* bacc = cnt + kP1Warps * B;         // [B]: this CTA's bucket totals over its tiles
-  uint32_t* red = bacc + B;                    // block scan scratch (16 words)
+  uint32_t* cnt = sm;                          // [B][kCntStride]: counts, then bases
+  uint32_t* bacc = cnt + B * kCntStride;       // [B]: this CTA's bucket totals over its tiles
+  uint32_t* red = bacc + B;                    // block scan scratch (32 words)
   // [kP1Tile] low parts of one tile, read as uint4: starts on a 16-byte boundary
   uint16_t* stage = reinterpret_cast<uint16_t*>(sm + p1_stage_words(B));
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t lowmask = (1u << L) - 1u;
+  const uint32_t ncnt = B * kCntStride;
   bool bad = false;
 
   for (uint32_t b = tid; b < B; b += kP1Threads) bacc[b] = 0;
 
   for (uint64_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
-    for (uint32_t i = tid; i < kP1Warps * B; i += kP1Threads) cnt[i] = 0;
-    __syncthreads();
+    for (uint32_t i = tid; i < ncnt; i += kP1Threads) cnt[i] = 0;
     const uint64_t base = t * kP1Tile;
     const uint32_t len = (uint32_t)((n - base) < kP1Tile ? (n - base) : kP1Tile);
     const uint32_t first = kP1Keys * tid;
-    const uint4* src = reinterpret_cast<const uint4*>(keys + base + first);
+    const bool full = first + kP1Keys <= len;
 
-    // this thread's consecutive keys; bit i of vm: key i is real and < U
     uint32_t kv[kP1Keys];
-    uint32_t vm = 0;
+    if (full) {
+      const uint4* src = reinterpret_cast<const uint4*>(keys + base + first);
 #pragma unroll
-    for (uint32_t i = 0; i < kP1Keys / 4; ++i) {
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (first + 4 * i + 3 < len) {
-        v = __ldg(src + i);
-      } else if (first + 4 * i < len) {
-        v.x = keys[base + first + 4 * i];
-        if (first + 4 * i + 1 < len) v.y = keys[base + first + 4 * i + 1];
-        if (first + 4 * i + 2 < len) v.z = keys[base + first + 4 * i + 2];
+      for (uint32_t i = 0; i < kP1Keys / 4; ++i) {
+        const uint4 v = __ldg(src + i);
+        kv[4 * i] = v.x;
+        kv[4 * i + 1] = v.y;
+        kv[4 * i + 2] = v.z;
+        kv[4 * i + 3] = v.w;
       }
-      kv[4 * i] = v.x;
-      kv[4 * i + 1] = v.y;
-      kv[4 * i + 2] = v.z;
-      kv[4 * i + 3] = v.w;
-    }
+    } else {
 #pragma unroll
-    for (uint32_t i = 0; i < kP1Keys; ++i) {
-      const bool real = first + i < len;
-      const bool ok = kv[i] < U;
-      bad |= real && !ok;
-      vm |= (real && ok) ? (1u << i) : 0u;
+      for (uint32_t i = 0; i < kP1Keys; ++i) kv[i] = first + i < len ? keys[base + first + i] : 0u;
     }
-    // Runs of one bucket pay off only when they are common (skew, sorted
-    // input, repeated keys); the warp decides together how it ingests the tile.
-    uint32_t same = 0;  // bit i: key i continues the bucket of key i - 1
+    // bit i of vm: key i is real and < U (all 16 in the common case, found with one max)
+    uint32_t mx = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < kP1Keys; ++i) mx = max(mx, kv[i]);
+    uint32_t vm = 0xffffu;
+    if (!full || mx >= U) {
+      vm = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < kP1Keys; ++i) {
+        const bool real = first + i < len;
+        const bool ok = kv[i] < U;
+        bad |= real && !ok;
+        vm |= (real && ok) ? (1u << i) : 0u;
+      }
+    }
+    // bit i of same: key i continues the bucket of key i - 1
+    uint32_t same = 0;
 #pragma unroll
     for (uint32_t i = 1; i < kP1Keys; ++i) same |= ((kv[i] >> L) == (kv[i - 1] >> L)) ? (1u << i) : 0u;
     same &= vm & (vm << 1);
     const bool runs = __popc(__ballot_sync(0xffffffffu, same != 0)) >= 16;
-    uint32_t* wcnt = cnt + warp * B;
+    __syncthreads();  // counters zeroed; the previous tile's stage is copied out
+
+    // ranks, two 16-bit ranks per register (a (bucket, warp) counter stays below 512)
+    uint32_t rk[kP1Keys / 2];
+#pragma unroll
+    for (uint32_t i = 0; i < kP1Keys / 2; ++i) rk[i] = 0;
     if (runs) {
+      uint32_t r = 0;
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
-        if (((vm >> i) & 1u) && !((same >> i) & 1u))  // a run starts here; its length counts the ones after it
-          atomicAdd(wcnt + (kv[i] >> L), (uint32_t)__ffs(~(same >> (i + 1))));
+        if ((vm >> i) & 1u) {
+          if (!((same >> i) & 1u))  // a run starts here; its length counts the ones after it
+            r = atomicAdd(cnt + (kv[i] >> L) * kCntStride + warp, (uint32_t)__ffs(~(same >> (i + 1))));
+          else
+            ++r;
+        }
+        rk[i / 2] |= r << (16 * (i & 1));
       }
-    } else {
+    } else if (vm == 0xffffu) {
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i)
-        if ((vm >> i) & 1u) atomicAdd(wcnt + (kv[i] >> L), 1u);
+        rk[i / 2] |= atomicAdd(cnt + (kv[i] >> L) * kCntStride + warp, 1u) << (16 * (i & 1));
+    } else {
+#pragma unroll
+      for (uint32_t i = 0; i < kP1Keys; ++i) {
+        const uint32_t r = ((vm >> i) & 1u) ? atomicAdd(cnt + (kv[i] >> L) * kCntStride + warp, 1u) : 0u;
+        rk[i / 2] |= r << (16 * (i & 1));
+      }
     }
     __syncthreads();
 
@@ -125,7 +152,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t
     const uint32_t per = (E + kP1Threads - 1) / kP1Threads;
     const uint32_t e0 = min(tid * per, E), e1 = min(e0 + per, E);
     uint32_t local = 0;
-    for (uint32_t e = e0; e < e1; ++e) local += cnt[(e % kP1Warps) * B + e / kP1Warps];
+    for (uint32_t e = e0; e < e1; ++e) local += cnt[(e / kP1Warps) * kCntStride + e % kP1Warps];
     uint32_t x = local;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -136,19 +163,19 @@ __global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t
     __syncthreads();
     if (warp == 0) {
       const uint32_t w0 = lane < kP1Warps ? red[lane] : 0u;
-      uint32_t s = w0;
+      uint32_t sum = w0;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
-        if (lane >= (uint32_t)d) s += y;
+        const uint32_t y = __shfl_up_sync(0xffffffffu, sum, d);
+        if (lane >= (uint32_t)d) sum += y;
       }
-      if (lane < kP1Warps) red[lane] = s - w0;
-      if (lane == kP1Warps - 1) red[kP1Warps] = s;  // valid keys of the tile
+      if (lane < kP1Warps) red[lane] = sum - w0;
+      if (lane == kP1Warps - 1) red[kP1Warps] = sum;  // valid keys of the tile
     }
     __syncthreads();
     uint32_t acc = red[warp] + (x - local);
     for (uint32_t e = e0; e < e1; ++e) {
-      uint32_t* c = &cnt[(e % kP1Warps) * B + e / kP1Warps];
+      uint32_t* c = &cnt[(e / kP1Warps) * kCntStride + e % kP1Warps];
       const uint32_t v = *c;
       *c = acc;
       acc += v;
@@ -158,29 +185,25 @@ __global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t
     const uint32_t tile_valid = red[kP1Warps];
     uint16_t* trow = toff + t * (uint64_t)(B + 1);
     for (uint32_t b = tid; b <= B; b += kP1Threads) {
-      const uint32_t start = b < B ? cnt[b] : tile_valid;
+      const uint32_t start = b < B ? cnt[b * kCntStride] : tile_valid;
       trow[b] = (uint16_t)start;
-      if (b < B) bacc[b] += (b + 1 < B ? cnt[b + 1] : tile_valid) - start;
+      if (b < B) bacc[b] += (b + 1 < B ? cnt[(b + 1) * kCntStride] : tile_valid) - start;
     }
-    __syncthreads();  // the bases are read above before the cursors move below
-    // each run takes its positions with one atomic on its (warp, bucket) cursor
-    if (runs) {
-      uint32_t pos = 0;
+    // every key to its slot: base of its (bucket, warp) + its rank
+    if (vm == 0xffffu) {
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
-        if ((vm >> i) & 1u) {
-          if (!((same >> i) & 1u)) {
-            pos = atomicAdd(wcnt + (kv[i] >> L), (uint32_t)__ffs(~(same >> (i + 1))));
-          } else {
-            ++pos;
-          }
-          stage[pos] = (uint16_t)(kv[i] & lowmask);
-        }
+        const uint32_t r = (rk[i / 2] >> (16 * (i & 1))) & 0xffffu;
+        stage[cnt[(kv[i] >> L) * kCntStride + warp] + r] = (uint16_t)(kv[i] & lowmask);
       }
     } else {
 #pragma unroll
-      for (uint32_t i = 0; i < kP1Keys; ++i)
-        if ((vm >> i) & 1u) stage[atomicAdd(wcnt + (kv[i] >> L), 1u)] = (uint16_t)(kv[i] & lowmask);
+      for (uint32_t i = 0; i < kP1Keys; ++i) {
+        if ((vm >> i) & 1u) {
+          const uint32_t r = (rk[i / 2] >> (16 * (i & 1))) & 0xffffu;
+          stage[cnt[(kv[i] >> L) * kCntStride + warp] + r] = (uint16_t)(kv[i] & lowmask);
+        }
+      }
     }
     __syncthreads();
     // write the grouped low parts: tile t owns low[t * 8192 ...]
@@ -188,9 +211,9 @@ __global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t
     uint4* dst = reinterpret_cast<uint4*>(low + t * kP1Tile);
     const uint4* st4 = reinterpret_cast<const uint4*>(stage);
     for (uint32_t v = tid; v < vecs; v += kP1Threads) dst[v] = st4[v];
-    __syncthreads();
   }
   if (bad) raise_error(err, ERRBIT_KEY_RANGE);
+  __syncthreads();
   for (uint32_t b = tid; b < B; b += kP1Threads)
     if (bacc[b]) red_add_global(btot + b, bacc[b]);
 }
@@ -293,124 +316,145 @@ __global__ void __launch_bounds__(1024) split_kernel(const uint16_t* __restrict_
 }
 
 // ------------------------------------------------------------------ pass 2
-// The CTA takes the item's tiles 512 at a time (one per thread): each thread
-// reads its tile's segment bounds for this bucket, and a CTA scan turns
-// segment lengths in 8-key blocks into one flat block range.  Every warp takes
-// an equal slice of that range (lane l: blocks l, l + 32, ...), finds its
-// first tile by binary search over the scan and then walks forward, so a few
-// very long segments (a hot bucket) keep every warp busy just like many short
-// ones.  Each lane keeps kP2Unroll block loads in flight before ingesting.
+// Two ways to spread an item's chunks (16-byte pieces of its segments) over
+// the warps, chosen per item from the mean segment length:
+//   short segments (uniform keys: ~9 chunks per tile): warp w takes the
+//     item's tiles 32 at a time (lane l: one tile); the chunks of those 32
+//     segments are numbered flat (a warp scan) and lane l takes chunks l,
+//     l + 32, ..., finding each chunk's tile by a 5-step binary search over
+//     the scan held in the lanes;
+//   long segments (a hot bucket, sorted or repeated keys): warp w takes
+//     tiles w, w + 16, ... and its lanes stride through each segment.
+// Either way every lane has chunks to load.  Low parts need no range check:
+// pass 1 dropped every key >= U.
 constexpr uint32_t kP2Threads = 512;
+constexpr uint32_t kP2Warps = kP2Threads / 32;
 constexpr uint32_t kP2Unroll = 4;
+constexpr uint32_t kP2LongSegment = 16;  // mean chunks per tile from which a warp takes one tile at a time
 
-struct BucketSmem {
-  uint32_t excl[kP2Threads + 1];   // exclusive block counts of the chunk's tiles
-  uint32_t seg0[kP2Threads];       // segment start (tile-relative), per tile
-  uint32_t seg1[kP2Threads];       // segment end
-  uint32_t red[kP2Threads / 32 + 1];
-};
+template <int MODE>
+__device__ __forceinline__ void count_chunk(const Sink<MODE>& s, const uint4& q, uint32_t vm) {
+  const uint32_t k[8] = {q.x & 0xffffu, q.x >> 16, q.y & 0xffffu, q.y >> 16,
+                         q.z & 0xffffu, q.z >> 16, q.w & 0xffffu, q.w >> 16};
+  if (vm == 0xffu && q.x == q.y && q.x == q.z && q.x == q.w && k[0] == k[1]) {
+    s.add(k[0], 8u);  // eight equal low parts (a hot or repeated key): one add
+  } else {
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i)
+      if ((vm >> i) & 1u) s.add(k[i], 1u);
+  }
+}
+
+// bits [from, to) of the chunk starting at tile position p0 that lie in the segment [a0, a1)
+__device__ __forceinline__ uint32_t chunk_mask(uint32_t a0, uint32_t a1, uint32_t p0) {
+  const uint32_t from = a0 > p0 ? a0 - p0 : 0u;
+  const uint32_t to = a1 - p0 < 8u ? a1 - p0 : 8u;
+  return ((1u << to) - 1u) & ~((1u << from) - 1u);
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(kP2Threads, 2) bucket_kernel(const uint16_t* __restrict__ low,
                                                                const uint16_t* __restrict__ toff, uint32_t B,
                                                                uint32_t L, uint32_t U, uint32_t* __restrict__ H,
                                                                const Item* __restrict__ items,
-                                                               const uint32_t* nitems, uint32_t crn_mode,
-                                                               uint32_t words_per_copy, uint32_t* err) {
+                                                               const uint32_t* nitems, uint32_t words_per_copy) {
   extern __shared__ __align__(16) uint32_t sh[];
-  __shared__ BucketSmem bs;
+  __shared__ uint32_t s_red[kP2Warps];
   if (blockIdx.x >= *nitems) return;
   const Item it = items[blockIdx.x];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint64_t b_lo = (uint64_t)it.bucket << L;
   const uint32_t Ub = (uint32_t)(((uint64_t)U - b_lo) < (1ull << L) ? ((uint64_t)U - b_lo) : (1ull << L));
   zero_smem(sh, words_per_copy);
+  // the item's chunk count, to pick the mapping
+  uint32_t mine = 0;
+  for (uint64_t t = it.t0 + tid; t < it.t1; t += kP2Threads) {
+    const uint16_t* row = toff + t * (uint64_t)(B + 1);
+    const uint32_t a0 = row[it.bucket], a1 = row[it.bucket + 1];
+    mine += a1 > a0 ? ((a1 + 7u) >> 3) - (a0 >> 3) : 0u;
+  }
+  mine = __reduce_add_sync(0xffffffffu, mine);
+  if (lane == 0) s_red[warp] = mine;
+  __syncthreads();
+  uint64_t chunks = 0;
+#pragma unroll
+  for (uint32_t w = 0; w < kP2Warps; ++w) chunks += s_red[w];
+  const bool long_segments = chunks >= (uint64_t)kP2LongSegment * (it.t1 - it.t0);
   const Sink<MODE> s{sh, H + b_lo, Ub, 0u};
-  bool bad = false;
-  uint32_t score = 0;
   const uint4* low4 = reinterpret_cast<const uint4*>(low);
 
-  for (uint64_t c = it.t0; c < it.t1; c += kP2Threads) {
-    // this thread's tile: segment bounds and length in 8-key blocks
-    const uint64_t t = c + tid;
-    uint32_t a0 = 0, a1 = 0, nb = 0;
-    if (t < it.t1) {
+  if (long_segments) {
+    for (uint64_t t = it.t0 + warp; t < it.t1; t += kP2Warps) {
       const uint16_t* row = toff + t * (uint64_t)(B + 1);
-      a0 = row[it.bucket];
-      a1 = row[it.bucket + 1];
-      nb = a1 > a0 ? (a1 + 7) / 8 - a0 / 8 : 0u;
-    }
-    uint32_t x = nb;
+      const uint32_t a0 = row[it.bucket], a1 = row[it.bucket + 1];
+      if (a1 <= a0) continue;
+      const uint32_t c_end = (a1 + 7u) >> 3;
+      const uint4* tile4 = low4 + t * (uint64_t)(kP1Tile / 8);
+      for (uint32_t c0 = (a0 >> 3) + lane; c0 < c_end; c0 += 32u * kP2Unroll) {
+        uint4 q[kP2Unroll];
+        uint32_t vm[kP2Unroll];
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane >= (uint32_t)d) x += y;
+        for (uint32_t u = 0; u < kP2Unroll; ++u) {
+          const uint32_t c = c0 + 32u * u;
+          vm[u] = 0;
+          q[u] = make_uint4(0u, 0u, 0u, 0u);
+          if (c < c_end) {
+            vm[u] = chunk_mask(a0, a1, c * 8u);
+            q[u] = __ldg(tile4 + c);
+          }
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u]);
+      }
     }
-    if (lane == 31) bs.red[warp] = x;
-    __syncthreads();  // also orders the smem histogram's zeroing before the first add
-    if (warp == 0) {
-      const uint32_t w0 = lane < kP2Threads / 32 ? bs.red[lane] : 0u;
-      uint32_t sum = w0;
+  } else {
+    for (uint64_t tb = it.t0 + (uint64_t)warp * 32u; tb < it.t1; tb += kP2Warps * 32u) {
+      // this lane's tile: the bucket's segment [a0, a1) and its chunks [a0 / 8, ceil(a1 / 8))
+      const uint64_t t = tb + lane;
+      uint32_t a0 = 0, a1 = 0;
+      if (t < it.t1) {
+        const uint16_t* row = toff + t * (uint64_t)(B + 1);
+        a0 = row[it.bucket];
+        a1 = row[it.bucket + 1];
+      }
+      const uint32_t nb = a1 > a0 ? ((a1 + 7u) >> 3) - (a0 >> 3) : 0u;
+      uint32_t incl = nb;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, sum, d);
-        if (lane >= (uint32_t)d) sum += y;
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= (uint32_t)d) incl += y;
       }
-      if (lane < kP2Threads / 32) bs.red[lane] = sum - w0;
-      if (lane == kP2Threads / 32 - 1) bs.excl[kP2Threads] = sum;
-    }
-    __syncthreads();
-    bs.excl[tid] = bs.red[warp] + (x - nb);
-    bs.seg0[tid] = a0;
-    bs.seg1[tid] = a1;
-    __syncthreads();
-    const uint32_t total = bs.excl[kP2Threads];
-    const uint32_t ntiles = (it.t1 - c) < kP2Threads ? (uint32_t)(it.t1 - c) : kP2Threads;
-    // warp w takes the flat block range [wb0, wb1); lane l starts at block wb0 + l
-    const uint32_t per_warp = ((total + kP2Threads / 32 - 1) / (kP2Threads / 32) + 31) & ~31u;
-    const uint32_t wb0 = min(warp * per_warp, total), wb1 = min(wb0 + per_warp, total);
-    uint32_t tile_i = 0;  // chunk tile holding this lane's next block (found once, then walked)
-    {
-      const uint32_t j = wb0 + lane;
-      uint32_t lo = 0, hi = ntiles - 1;
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (bs.excl[mid] <= j)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      tile_i = lo;
-    }
-    for (uint32_t j0 = wb0; j0 < wb1; j0 += 32 * kP2Unroll) {
-      uint4 q[kP2Unroll];
-      uint32_t vm[kP2Unroll];
+      const uint32_t excl = incl - nb;
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      for (uint32_t j0 = 0; j0 < total; j0 += 32u * kP2Unroll) {
+        uint4 q[kP2Unroll];
+        uint32_t vm[kP2Unroll];
 #pragma unroll
-      for (uint32_t u = 0; u < kP2Unroll; ++u) {
-        const uint32_t j = j0 + u * 32 + lane;
-        vm[u] = 0;
-        q[u] = make_uint4(0u, 0u, 0u, 0u);
-        if (j < wb1) {
-          while (tile_i + 1 < ntiles && bs.excl[tile_i + 1] <= j) ++tile_i;
-          const uint32_t s0 = bs.seg0[tile_i], s1 = bs.seg1[tile_i];
-          const uint32_t blk_in_tile = s0 / 8 + (j - bs.excl[tile_i]);  // 8-key block within the tile
-          const uint32_t p0 = blk_in_tile * 8;                            // its first key, tile-relative
-          const uint32_t from = s0 > p0 ? s0 - p0 : 0u;
-          const uint32_t to = s1 - p0 < 8 ? s1 - p0 : 8u;
-          vm[u] = ((1u << to) - 1u) & ~((1u << from) - 1u);
-          q[u] = ld_stream_v4(low4 + ((c + tile_i) * (kP1Tile / 8) + blk_in_tile));
+        for (uint32_t u = 0; u < kP2Unroll; ++u) {
+          const uint32_t j = j0 + u * 32u + lane;
+          // the chunk's tile: the last lane l with excl_l <= j (lanes with no chunks are never it)
+          uint32_t l = 0;
+#pragma unroll
+          for (uint32_t step = 16; step != 0; step >>= 1) {
+            const uint32_t e = __shfl_sync(0xffffffffu, excl, l + step);
+            if (e <= j) l += step;
+          }
+          const uint32_t sa = __shfl_sync(0xffffffffu, a0, l);
+          const uint32_t sb = __shfl_sync(0xffffffffu, a1, l);
+          const uint32_t el = __shfl_sync(0xffffffffu, excl, l);
+          vm[u] = 0;
+          q[u] = make_uint4(0u, 0u, 0u, 0u);
+          if (j < total) {
+            const uint32_t c = (sa >> 3) + (j - el);  // chunk within the tile
+            vm[u] = chunk_mask(sa, sb, c * 8u);
+            q[u] = __ldg(low4 + (tb + l) * (uint64_t)(kP1Tile / 8) + c);
+          }
         }
-      }
 #pragma unroll
-      for (uint32_t u = 0; u < kP2Unroll; ++u) {
-        const uint32_t k[8] = {q[u].x & 0xffffu, q[u].x >> 16, q[u].y & 0xffffu, q[u].y >> 16,
-                               q[u].z & 0xffffu, q[u].z >> 16, q[u].w & 0xffffu, q[u].w >> 16};
-        ingest_masked<8, MODE>(k, vm[u], s, Ub, bad, crn_mode, score);
+        for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u]);
       }
     }
-    __syncthreads();  // the chunk's tables are rewritten next round
   }
-  if (bad) raise_error(err, ERRBIT_KEY_RANGE);
   __syncthreads();
   flush_smem<MODE>(sh, 1, words_per_copy, Ub, H + b_lo, false);
 }
@@ -460,6 +504,7 @@ bool two_level_fits(uint64_t n, uint32_t U, uint32_t key_bytes, const void* keys
 cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* ws,
                              const TwoLevelLayout& T, uint32_t crn_mode, const DeviceInfo& dev, uint32_t* err,
                              cudaStream_t stream, bool accumulate) {
+  (void)crn_mode;  // runs are merged by each pass itself
   char* base = static_cast<char*>(ws);
   uint16_t* low = reinterpret_cast<uint16_t*>(base + T.off_low);
   uint16_t* toff = reinterpret_cast<uint16_t*>(base + T.off_toff);
@@ -477,7 +522,7 @@ cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   if (e != cudaSuccess) return e;
   const uint64_t grid1 = std::min<uint64_t>(T.num_tiles, (uint64_t)dev.sms * std::max(per_sm, 1));
   partition_kernel<<<(unsigned)grid1, kP1Threads, p1_smem, stream>>>(keys, n, U, T.L, T.B, T.num_tiles, low, toff,
-                                                                    btot, err, crn_mode);
+                                                                    btot, err);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   uint32_t* pbase = reinterpret_cast<uint32_t*>(base + T.off_pbase);
   plan_kernel<<<1, 1024, 0, stream>>>(btot, T.B, T.item_keys, pbase, nitems);
@@ -496,10 +541,10 @@ cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   }
   const uint16_t* lowc = low;
   const uint16_t* toffc = toff;
-  uint32_t B = T.B, L = T.L, UU = U, crn = crn_mode, wpc = T.words_per_copy;
+  uint32_t B = T.B, L = T.L, UU = U, wpc = T.words_per_copy;
   const Item* itc = items;
   const uint32_t* nic = nitems;
-  void* args[] = {&lowc, &toffc, &B, &L, &UU, &H, &itc, &nic, &crn, &wpc, &err};
+  void* args[] = {&lowc, &toffc, &B, &L, &UU, &H, &itc, &nic, &wpc};
   return cudaLaunchKernel(fn, dim3((unsigned)T.max_items), dim3(p2_threads), args, p2_smem, stream);
 }
 

@@ -63,6 +63,12 @@ cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint3
                              const TwoLevelLayout& T, uint32_t crn_mode, const DeviceInfo& dev, uint32_t* err,
                              cudaStream_t stream, bool accumulate);
 
+// Self-tests of the bounded device waits (a wait that is made to run out).
+size_t offsets_selftest_bytes();
+cudaError_t launch_offsets_selftest(void* ws, uint32_t* err, cudaStream_t stream);
+size_t radix_selftest_bytes();
+cudaError_t launch_radix_selftest(void* ws, uint32_t* err, cudaStream_t stream);
+
 // Step 2.  reconstruct.cu
 constexpr uint32_t kChunkBins = 1024;  // bins per offset-scan chunk
 constexpr uint32_t kTileKeys = 8192;   // output keys per expansion tile

@@ -1,0 +1,435 @@
+// DialSort-Radix (Sec. "Full int32 range"): LSD radix sort in base 256, four
+// passes, each pass a DialSort step on one 8-bit digit -- count the digit
+// (Eq. (1) with U = 256) and place every key at its digit's cursor (Eq. (2)'s
+// projection, carrying the key instead of the digit).  LSD needs each pass to
+// be stable, so placement keeps input order among equal digits.  Signed keys
+// sort by flipping the sign bit of the top digit.  Keys are only ever split
+// into digits; no two keys are compared by magnitude.
+//
+// GPU layout of one pass (one kernel, tiles of 8192 keys taken in ticket
+// order):
+//   * warp w of the CTA holds keys [512 w, 512 w + 512) of the tile, lane l
+//     key 32 i + l in step i, so the order (step, lane) is input order;
+//   * in each step the warp finds the lanes with the same digit from 8
+//     ballots (one per digit bit) and ranks them by lane: a stable rank with
+//     no atomics; per-warp digit counters carry the rank across steps;
+//   * a scan over (digit, warp) gives each key its slot in the tile's stable
+//     digit order; keys are staged there in shared memory;
+//   * the tile's per-digit counts are chained to the earlier tiles' by a
+//     decoupled look-back (one thread per digit), giving every digit run of
+//     the tile its global start = digit base + keys of that digit in earlier
+//     tiles;
+//   * the staged keys are written out, runs of one digit to consecutive
+//     addresses.
+// The global digit bases come from a histogram of the pass's digit over all
+// keys: the first digit's from a separate counting kernel, the others counted
+// by the previous pass while it has the keys in hand.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace dialsort {
+namespace {
+
+constexpr uint32_t kRxThreads = 512;
+constexpr uint32_t kRxWarps = kRxThreads / 32;
+constexpr uint32_t kRxSteps = 16;                       // keys per thread
+constexpr uint32_t kRxTile = kRxThreads * kRxSteps;     // 8192 keys per tile
+constexpr uint32_t kRxDigits = 256;
+constexpr uint32_t kRxPasses = 4;
+
+// Look-back descriptors: (state << 32) | value.  Pass p publishes state 2p+1
+// (the tile's own count of the digit) and 2p+2 (count of the digit in tiles
+// 0..t); anything else is "not yet" for pass p, so one zeroing per sort
+// serves all four passes.
+__device__ __forceinline__ uint64_t rx_desc(uint32_t state, uint32_t value) {
+  return ((uint64_t)state << 32) | value;
+}
+
+__device__ __forceinline__ uint32_t rx_digit(uint32_t x, uint32_t pass, bool is_signed) {
+  const uint32_t d = (x >> (8u * pass)) & 0xffu;
+  return (is_signed && pass == kRxPasses - 1) ? (d ^ 0x80u) : d;  // two's complement order
+}
+
+// Add 1 to h[d] for every lane; when all 32 lanes hold the same digit (keys
+// that share a byte: small keys, a constant top byte) one lane adds 32.
+__device__ __forceinline__ void rx_count(uint32_t* h, uint32_t d, uint32_t lane) {
+  const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+  if (__all_sync(0xffffffffu, d == d0)) {
+    if (lane == 0) atomicAdd(h + d, 32u);
+  } else {
+    atomicAdd(h + d, 1u);
+  }
+}
+
+// Digit-0 histogram of all keys: shared counters (one copy per group of four
+// warps), merged into ghist[0].
+__global__ void __launch_bounds__(kRxThreads) rx_count_kernel(const uint32_t* __restrict__ keys, uint64_t n,
+                                                               uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[4][kRxDigits];
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  for (uint32_t i = tid; i < 4 * kRxDigits; i += kRxThreads) (&h[0][0])[i] = 0;
+  __syncthreads();
+  uint32_t* mine = h[warp & 3u];
+  // scalar head up to the first 16-byte boundary, 16-byte body, scalar tail
+  const uint64_t mis = (reinterpret_cast<uintptr_t>(keys) & 15u) / 4u;
+  const uint64_t head = mis ? ((4u - mis) < n ? (4u - mis) : n) : 0u;
+  const uint64_t nvec = (n - head) / 4;
+  const uint4* k4 = reinterpret_cast<const uint4*>(keys + head);
+  const uint64_t stride = (uint64_t)gridDim.x * kRxThreads;
+  const uint64_t vend = (nvec + 31u) & ~31ull;  // whole warps iterate together
+  for (uint64_t v = (uint64_t)blockIdx.x * kRxThreads + tid; v < vend; v += stride) {
+    if (v < nvec) {
+      const uint4 q = ld_stream_v4(k4 + v);
+      if (__activemask() == 0xffffffffu) {
+        rx_count(mine, q.x & 0xffu, lane);
+        rx_count(mine, q.y & 0xffu, lane);
+        rx_count(mine, q.z & 0xffu, lane);
+        rx_count(mine, q.w & 0xffu, lane);
+      } else {
+        atomicAdd(mine + (q.x & 0xffu), 1u);
+        atomicAdd(mine + (q.y & 0xffu), 1u);
+        atomicAdd(mine + (q.z & 0xffu), 1u);
+        atomicAdd(mine + (q.w & 0xffu), 1u);
+      }
+    }
+  }
+  if (blockIdx.x == 0) {
+    const uint64_t tail0 = head + nvec * 4;
+    for (uint64_t i = tid; i < head + (n - tail0); i += kRxThreads)
+      atomicAdd(mine + (keys[i < head ? i : tail0 + (i - head)] & 0xffu), 1u);
+  }
+  __syncthreads();
+  for (uint32_t d = tid; d < kRxDigits; d += kRxThreads) {
+    const uint32_t c = h[0][d] + h[1][d] + h[2][d] + h[3][d];
+    if (c) red_add_global(ghist + d, c);
+  }
+}
+
+struct RxSmem {
+  uint32_t in[kRxTile];                  // the tile's keys in input order (frees registers across the scan)
+  uint32_t stage[kRxTile];               // the tile's keys in stable digit order
+  uint16_t wcnt[kRxWarps][kRxDigits];    // per-warp digit counters, then per-warp digit bases
+  uint32_t tstart[kRxDigits + 1];        // digit starts within the tile
+  uint32_t gpos[kRxDigits];              // global position of the tile's first key of each digit
+  uint32_t gbase[kRxDigits];             // global start of each digit
+  uint32_t next[kRxDigits];              // histogram of the next pass's digit (this CTA)
+  uint32_t red[32];
+  uint32_t tile;
+};
+
+// Exclusive scan of v over the first 256 threads (the others pass through); returns the prefix.
+__device__ __forceinline__ uint32_t scan256(uint32_t v, uint32_t* red, uint32_t* total) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= (uint32_t)d) x += y;
+  }
+  if (lane == 31 && warp < kRxDigits / 32) red[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w0 = lane < kRxDigits / 32 ? red[lane] : 0u;
+    uint32_t s = w0;
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
+      if (lane >= (uint32_t)d) s += y;
+    }
+    if (lane < kRxDigits / 32) red[lane] = s - w0;
+    if (lane == kRxDigits / 32 - 1) red[kRxDigits / 32] = s;
+  }
+  __syncthreads();
+  const uint32_t r = warp < kRxDigits / 32 ? red[warp] + (x - v) : 0u;
+  *total = red[kRxDigits / 32];
+  __syncthreads();
+  return r;
+}
+
+template <bool kSigned>
+__global__ void __launch_bounds__(kRxThreads, 2) rx_pass_kernel(const uint32_t* __restrict__ src,
+                                                                uint32_t* __restrict__ dst, uint64_t n,
+                                                                uint32_t pass, uint64_t num_tiles,
+                                                                uint32_t* __restrict__ ghist,
+                                                                uint64_t* __restrict__ desc,
+                                                                uint32_t* __restrict__ tickets, uint32_t* err) {
+  extern __shared__ __align__(16) unsigned char rx_raw[];
+  RxSmem& S = *reinterpret_cast<RxSmem*>(rx_raw);
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const bool count_next = pass + 1 < kRxPasses;
+
+  // global digit starts of this pass: exclusive scan of its histogram
+  {
+    uint32_t total;
+    const uint32_t c = tid < kRxDigits ? ghist[pass * kRxDigits + tid] : 0u;
+    const uint32_t ex = scan256(c, S.red, &total);
+    if (tid < kRxDigits) {
+      S.gbase[tid] = ex;
+      S.next[tid] = 0;
+    }
+  }
+  bool timed_out = false;
+
+  for (;;) {
+    if (tid == 0) S.tile = atomicAdd(tickets + pass, 1u);
+    for (uint32_t i = tid; i < kRxWarps * kRxDigits / 2; i += kRxThreads)
+      reinterpret_cast<uint32_t*>(&S.wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t t = S.tile;
+    if (t >= num_tiles) break;
+    const uint64_t base = t * kRxTile + (uint64_t)warp * (kRxSteps * 32u);
+
+    // load (striped: step i, lane l -> key 32 i + l of the warp's 512) and rank stably
+    uint32_t kv[kRxSteps];
+    uint32_t* in = S.in + warp * (kRxSteps * 32u) + lane;
+#pragma unroll
+    for (uint32_t i = 0; i < kRxSteps; ++i) {
+      const uint64_t p = base + 32u * i + lane;
+      kv[i] = p < n ? src[p] : 0u;
+      in[32u * i] = kv[i];
+    }
+    uint32_t rk[kRxSteps / 2];
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (uint32_t i = 0; i < kRxSteps; ++i) {
+      const bool valid = base + 32u * i + lane < n;
+      const uint32_t d = rx_digit(kv[i], pass, kSigned);
+      uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (uint32_t b = 0; b < 8; ++b) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? m : ~m;
+      }
+      const uint32_t before = S.wcnt[warp][d];
+      const uint32_t r = before + __popc(peers & lt);
+      __syncwarp();
+      if (valid && (peers & lt) == 0) S.wcnt[warp][d] = (uint16_t)(before + __popc(peers));
+      __syncwarp();
+      if (i % 2 == 0)
+        rk[i / 2] = r;
+      else
+        rk[i / 2] |= r << 16;
+    }
+    if (count_next) {  // the next pass's digit, from the keys kept in shared memory
+#pragma unroll 4
+      for (uint32_t i = 0; i < kRxSteps; ++i) {
+        const bool valid = base + 32u * i + lane < n;
+        const uint32_t dn = rx_digit(in[32u * i], pass + 1, kSigned);
+        const uint32_t d0 = __shfl_sync(0xffffffffu, dn, 0);  // every lane takes part (no short circuit)
+        if (__all_sync(0xffffffffu, valid && dn == d0)) {
+          if (lane == 0) atomicAdd(&S.next[dn], 32u);
+        } else if (valid) {
+          atomicAdd(&S.next[dn], 1u);
+        }
+      }
+    }
+    __syncthreads();
+
+    // per digit: warp bases (in place) and the tile's count; then digit starts in the tile
+    uint32_t cnt = 0;
+    if (tid < kRxDigits) {
+#pragma unroll
+      for (uint32_t w = 0; w < kRxWarps; ++w) {
+        const uint32_t c = S.wcnt[w][tid];
+        S.wcnt[w][tid] = (uint16_t)cnt;
+        cnt += c;
+      }
+    }
+    uint32_t tile_valid;
+    const uint32_t start = scan256(cnt, S.red, &tile_valid);
+    if (tid < kRxDigits) {
+      S.tstart[tid] = start;
+      if (tid == 0) S.tstart[kRxDigits] = tile_valid;
+      // publish this tile's count, then look back over earlier tiles for the digit's prefix
+      uint64_t* my = desc + t * kRxDigits + tid;
+      const uint32_t agg = 2u * pass + 1u, inc = 2u * pass + 2u;
+      if (t == 0) {
+        st_release_u64(my, rx_desc(inc, cnt));
+        S.gpos[tid] = S.gbase[tid];
+      } else {
+        st_release_u64(my, rx_desc(agg, cnt));
+        uint32_t prefix = 0;
+        uint64_t tt = t - 1;
+        uint32_t spins = 0;
+        for (;;) {
+          const uint64_t v = ld_acquire_u64(desc + tt * kRxDigits + tid);
+          const uint32_t state = (uint32_t)(v >> 32);
+          if (state == inc) {
+            prefix += (uint32_t)v;
+            break;
+          }
+          if (state == agg) {
+            prefix += (uint32_t)v;
+            if (tt == 0) break;  // (tile 0 publishes inclusive only; kept for safety)
+            --tt;
+            continue;
+          }
+          if (++spins >= kSpinLimit) {  // predecessor never published: give up, report
+            timed_out = true;
+            break;
+          }
+          __nanosleep(64);
+        }
+        st_release_u64(my, rx_desc(inc, prefix + cnt));
+        S.gpos[tid] = S.gbase[tid] + prefix;
+      }
+    }
+    __syncthreads();
+
+    // stage every key at its slot in the tile's stable digit order
+#pragma unroll
+    for (uint32_t i = 0; i < kRxSteps; ++i) {
+      if (base + 32u * i + lane < n) {
+        const uint32_t x = in[32u * i];
+        const uint32_t d = rx_digit(x, pass, kSigned);
+        const uint32_t r = (rk[i / 2] >> (16 * (i & 1))) & 0xffffu;
+        S.stage[S.tstart[d] + S.wcnt[warp][d] + r] = x;
+      }
+    }
+    __syncthreads();
+    // write out: consecutive slots of one digit go to consecutive addresses
+    for (uint32_t j = tid; j < tile_valid; j += kRxThreads) {
+      const uint32_t x = S.stage[j];
+      const uint32_t d = rx_digit(x, pass, kSigned);
+      const uint64_t pos = (uint64_t)S.gpos[d] + (j - S.tstart[d]);
+      if (pos < n) dst[pos] = x;  // always true unless a look-back timed out
+    }
+    __syncthreads();
+  }
+  if (timed_out) raise_error(err, ERRBIT_TIMEOUT);
+  if (count_next) {
+    __syncthreads();
+    for (uint32_t d = tid; d < kRxDigits; d += kRxThreads)
+      if (S.next[d]) red_add_global(ghist + (pass + 1) * kRxDigits + d, S.next[d]);
+  }
+}
+
+struct RxLayout {
+  uint64_t num_tiles = 0;
+  size_t off_ghist = 0, off_tickets = 0, off_desc = 0, clear_bytes = 0, off_tmp = 0, total = 0;
+};
+
+RxLayout rx_layout(uint64_t n) {
+  RxLayout R;
+  R.num_tiles = (n + kRxTile - 1) / kRxTile;
+  size_t o = 0;
+  R.off_ghist = o;
+  o += 4 * (size_t)kRxPasses * kRxDigits;
+  R.off_tickets = o;
+  o = align_up(o + 4 * kRxPasses, 256);
+  R.off_desc = o;
+  o = align_up(o + 8 * (size_t)R.num_tiles * kRxDigits, 256);
+  R.clear_bytes = o;
+  R.off_tmp = o;
+  o = align_up(o + 4 * (size_t)n, 256);
+  R.total = o;
+  return R;
+}
+
+dialsort_status_t radix_impl(const uint32_t* keys, uint64_t n, uint32_t* out, void* ws, size_t ws_bytes,
+                             bool is_signed, cudaStream_t st) {
+  if (n >= (1ull << 32)) return DIALSORT_ERR_INVALID_ARG;
+  if (n > 0 && (keys == nullptr || out == nullptr)) return DIALSORT_ERR_INVALID_ARG;
+  if (((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(out)) & 3u) != 0)
+    return DIALSORT_ERR_INVALID_ARG;
+  const RxLayout R = rx_layout(n);
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < R.total)
+    return DIALSORT_ERR_WORKSPACE;
+  if (n == 0) return DIALSORT_OK;
+  const DeviceInfo* dev = device_info();
+  if (!dev) return DIALSORT_ERR_CUDA;
+  const void* kp;
+  const void* op;
+  dialsort_status_t s = kernel_address(keys, *dev, &kp);
+  if (s == DIALSORT_OK) s = kernel_address(out, *dev, &op);
+  if (s != DIALSORT_OK) return s;
+  keys = static_cast<const uint32_t*>(kp);
+  out = static_cast<uint32_t*>(const_cast<void*>(op));
+
+  char* base = static_cast<char*>(ws);
+  uint32_t* ghist = reinterpret_cast<uint32_t*>(base + R.off_ghist);
+  uint32_t* tickets = reinterpret_cast<uint32_t*>(base + R.off_tickets);
+  uint64_t* desc = reinterpret_cast<uint64_t*>(base + R.off_desc);
+  uint32_t* tmp = reinterpret_cast<uint32_t*>(base + R.off_tmp);
+  cudaError_t e = cudaMemsetAsync(base, 0, R.clear_bytes, st);
+  if (e != cudaSuccess) return DIALSORT_ERR_CUDA;
+  const unsigned cgrid = (unsigned)std::min<uint64_t>((n / 4 + kRxThreads - 1) / kRxThreads + 1,
+                                                      (uint64_t)dev->sms * 4);
+  rx_count_kernel<<<cgrid, kRxThreads, 0, st>>>(keys, n, ghist);
+  if (cudaGetLastError() != cudaSuccess) return DIALSORT_ERR_CUDA;
+
+  const void* fn = is_signed ? reinterpret_cast<const void*>(&rx_pass_kernel<true>)
+                             : reinterpret_cast<const void*>(&rx_pass_kernel<false>);
+  const size_t smem = sizeof(RxSmem);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return DIALSORT_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRxThreads, smem) != cudaSuccess)
+    return DIALSORT_ERR_CUDA;
+  // tiles go out in ticket order, so a tile waits only on tiles whose CTAs are already running
+  const unsigned grid = (unsigned)std::min<uint64_t>(R.num_tiles, (uint64_t)dev->sms * std::max(per_sm, 1));
+  // ping-pong: keys -> tmp -> out -> tmp -> out (out may be keys: pass 0 and the count read keys first)
+  const uint32_t* srcs[kRxPasses] = {keys, tmp, out, tmp};
+  uint32_t* dsts[kRxPasses] = {tmp, out, tmp, out};
+  uint64_t num_tiles = R.num_tiles;
+  for (uint32_t p = 0; p < kRxPasses; ++p) {
+    const uint32_t* sp = srcs[p];
+    uint32_t* dp = dsts[p];
+    uint32_t pass = p;
+    uint64_t nn = n;
+    uint32_t* err = dev->err;
+    void* args[] = {&sp, &dp, &nn, &pass, &num_tiles, &ghist, &desc, &tickets, &err};
+    if (cudaLaunchKernel(fn, dim3(grid), dim3(kRxThreads), args, smem, st) != cudaSuccess) return DIALSORT_ERR_CUDA;
+  }
+  return DIALSORT_OK;
+}
+
+}  // namespace
+
+// Self-test of the bounded look-back wait: one CTA runs pass 0 on tile 1 of
+// 2^14 keys (the ticket starts at 1), so tile 0 never publishes and the wait
+// for it runs out, recording ERRBIT_TIMEOUT.  Every write stays inside tmp.
+size_t radix_selftest_bytes() { return rx_layout(2 * kRxTile).total; }
+
+cudaError_t launch_radix_selftest(void* ws, uint32_t* err, cudaStream_t stream) {
+  const uint64_t n = 2 * kRxTile;
+  const RxLayout R = rx_layout(n);
+  char* base = static_cast<char*>(ws);
+  cudaError_t e = cudaMemsetAsync(base, 0, R.total, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + R.off_tickets, 1, 1, stream);  // pass 0's ticket = 1
+  if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(RxSmem);
+  e = cudaFuncSetAttribute(rx_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  uint32_t* tmp = reinterpret_cast<uint32_t*>(base + R.off_tmp);
+  rx_pass_kernel<false><<<1, kRxThreads, smem, stream>>>(tmp, tmp, n, 0u, R.num_tiles,
+                                                          reinterpret_cast<uint32_t*>(base + R.off_ghist),
+                                                          reinterpret_cast<uint64_t*>(base + R.off_desc),
+                                                          reinterpret_cast<uint32_t*>(base + R.off_tickets), err);
+  return cudaGetLastError();
+}
+
+namespace {
+}  // namespace
+}  // namespace dialsort
+
+using namespace dialsort;
+
+extern "C" {
+
+size_t dialsort_radix_workspace_size(uint64_t n) { return rx_layout(n).total; }
+
+dialsort_status_t dialsort_radix_sort_i32(const int32_t* keys, uint64_t n, int32_t* out, void* ws, size_t ws_bytes,
+                                          void* stream) {
+  return radix_impl(reinterpret_cast<const uint32_t*>(keys), n, reinterpret_cast<uint32_t*>(out), ws, ws_bytes,
+                    true, static_cast<cudaStream_t>(stream));
+}
+
+dialsort_status_t dialsort_radix_sort_u32(const uint32_t* keys, uint64_t n, uint32_t* out, void* ws,
+                                          size_t ws_bytes, void* stream) {
+  return radix_impl(keys, n, out, ws, ws_bytes, false, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -146,10 +146,55 @@ __host__ __device__ inline uint64_t offset_groups(uint64_t num_chunks) {
   return (num_chunks + kReconThreads / 32 - 1) / (kReconThreads / 32);
 }
 
+// Tiles crossed by at most this many short runs are painted run by run; others fill forward.
+// Runs of kLongRun slots or more (at most four per tile) are painted by the whole CTA.
+constexpr uint32_t kPaintRuns = 256;
+constexpr uint32_t kLongRun = kTileKeys / 4;
+
 struct ExpandSmem {
   uint32_t M[kTileKeys];  // key + 1 where a run starts, 0 elsewhere
   uint32_t red32[kReconThreads / 32 + 1];
+  uint32_t nruns;         // short runs that cross the tile
+  uint32_t nlong;         // long runs that cross the tile
+  uint2 runs[kPaintRuns]; // (first slot | end slot << 16, key) of each short run, in no order
+  uint2 longs[4];         // the same for the long runs
 };
+
+// Record a run crossing the tile: slots [s, e) hold key.
+__device__ __forceinline__ void note_run(ExpandSmem& sm, uint32_t s, uint32_t e, uint32_t key) {
+  if (e - s >= kLongRun) {
+    const uint32_t i = atomicAdd(&sm.nlong, 1u);
+    if (i < 4) sm.longs[i] = make_uint2(s | (e << 16), key);
+  } else {
+    const uint32_t i = atomicAdd(&sm.nruns, 1u);
+    if (i < kPaintRuns) sm.runs[i] = make_uint2(s | (e << 16), key);
+  }
+}
+
+// Slots [s, e) of the tile starting at dst get `key`: 16-byte stores over the aligned middle, plain
+// stores at the ends; called by `lanes` threads together (a warp, or the CTA), `lane` in [0, lanes).
+template <typename OutT>
+__device__ __forceinline__ void paint_run(OutT* __restrict__ dst, uint32_t s, uint32_t e, uint32_t key,
+                                          int out_aligned, uint32_t lane, uint32_t lanes) {
+  constexpr uint32_t kPer = 16 / sizeof(OutT);  // keys per 16-byte store
+  const uint32_t a = out_aligned ? (s + kPer - 1) / kPer * kPer : e;  // first aligned slot
+  const uint32_t b = out_aligned ? e / kPer * kPer : e;                // end of the aligned middle
+  if (a >= b) {  // no aligned middle: plain stores
+    for (uint32_t i = s + lane; i < e; i += lanes) dst[i] = (OutT)key;
+    return;
+  }
+  if (s + lane < a) dst[s + lane] = (OutT)key;  // head: fewer than kPer slots
+  uint4 v;
+  if (sizeof(OutT) == 4) {
+    v = make_uint4(key, key, key, key);
+  } else {
+    const uint32_t k2 = (key & 0xffffu) | (key << 16);
+    v = make_uint4(k2, k2, k2, k2);
+  }
+  uint4* d4 = reinterpret_cast<uint4*>(dst + a);
+  for (uint32_t q = lane; q < (b - a) / kPer; q += lanes) d4[q] = v;
+  if (b + lane < e) dst[b + lane] = (OutT)key;  // tail: fewer than kPer slots
+}
 
 // Output tile `tile` (keys [tile * 8192, ...)) of the projection.  Marks the
 // slot where each run starts (slot 0 gets the run covering the tile's first
@@ -170,6 +215,10 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
 
   uint4* M4 = reinterpret_cast<uint4*>(M);
   for (uint32_t i = tid; i < kTileKeys / 4; i += kReconThreads) M4[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) {
+    sm.nruns = 0;
+    sm.nlong = 0;
+  }
   __syncthreads();
 
   // Mark run starts of every chunk overlapping [tile_lo, tile_hi).  A dense
@@ -197,10 +246,14 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
         if (h[j] != 0) {
           const uint64_t start = oc + sc, end = start + h[j];
           const uint32_t mark = (uint32_t)(b0 + j) + 1u;
-          if (start >= tile_lo && start < tile_hi)
+          const uint32_t e = (uint32_t)((end < tile_hi ? end : tile_hi) - tile_lo);
+          if (start >= tile_lo && start < tile_hi) {
             M[start - tile_lo] = mark;
-          else if (start < tile_lo && end > tile_lo)
+            note_run(sm, (uint32_t)(start - tile_lo), e, mark - 1u);
+          } else if (start < tile_lo && end > tile_lo) {
             M[0] = mark;
+            note_run(sm, 0u, e, mark - 1u);
+          }
         }
         sc += h[j];
       }
@@ -230,10 +283,14 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
           if (h[j] != 0) {
             const uint64_t end = start + h[j];
             const uint32_t mark = (uint32_t)(b0 + j) + 1u;
-            if (start >= tile_lo && start < tile_hi)
+            const uint32_t e = (uint32_t)((end < tile_hi ? end : tile_hi) - tile_lo);
+            if (start >= tile_lo && start < tile_hi) {
               M[start - tile_lo] = mark;
-            else if (start < tile_lo && end > tile_lo)
+              note_run(sm, (uint32_t)(start - tile_lo), e, mark - 1u);
+            } else if (start < tile_lo && end > tile_lo) {
               M[0] = mark;
+              note_run(sm, 0u, e, mark - 1u);
+            }
           }
           start += h[j];
         }
@@ -242,6 +299,21 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
     }
   }
   __syncthreads();
+
+  OutT* dst = out + tile_lo;
+  const uint32_t nruns = sm.nruns, nlong = sm.nlong;
+  if (nruns <= kPaintRuns) {  // few runs: paint each with its key
+    for (uint32_t r = warp; r < nruns; r += kReconThreads / 32) {
+      const uint2 run = sm.runs[r];
+      paint_run<OutT>(dst, run.x & 0xffffu, run.x >> 16, run.y, out_aligned, lane, 32u);
+    }
+    for (uint32_t r = 0; r < nlong && r < 4; ++r) {
+      const uint2 run = sm.longs[r];
+      paint_run<OutT>(dst, run.x & 0xffffu, run.x >> 16, run.y, out_aligned, tid, kReconThreads);
+    }
+    __syncthreads();  // sm is reused by the caller's next item
+    return;
+  }
 
   // Fill forward: every slot takes the latest mark at or before it.  Warp w
   // owns slots [1024 w, 1024 w + 1024); in round r lane l holds the quad at
@@ -266,7 +338,6 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
   uint32_t carry = 0;  // rightmost mark of the warps before this one
   for (int w2 = (int)warp - 1; w2 >= 0 && carry == 0; --w2) carry = red32[w2];
 
-  OutT* dst = out + tile_lo;
   for (uint32_t r = 0; r < kRounds; ++r) {
     const uint32_t slot = warp * kWarpSlots + r * 128 + lane * 4;
     uint4 q = M4[wq + r * 32 + lane];

@@ -71,6 +71,27 @@ ReconLayout recon_layout(uint32_t U, uint64_t n) {
   return L;
 }
 
+// Self-test of the bounded look-back wait: one CTA scans group 1 of a 16-chunk
+// histogram whose group 0 is never scanned (the ticket starts at 1), so its
+// wait for group 0's descriptor runs out and records ERRBIT_TIMEOUT.
+size_t offsets_selftest_bytes() { return recon_layout(16 * kChunkBins, 0).total + 4 * 16 * (size_t)kChunkBins; }
+
+cudaError_t launch_offsets_selftest(void* ws, uint32_t* err, cudaStream_t stream) {
+  const uint32_t U = 16 * kChunkBins;
+  const ReconLayout L = recon_layout(U, 0);
+  char* base = static_cast<char*>(ws);
+  uint32_t* H = reinterpret_cast<uint32_t*>(base + L.total);
+  cudaError_t e = cudaMemsetAsync(base, 0, L.total + 4 * (size_t)U, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + L.off_ticket, 1, 1, stream);  // ticket = 1
+  if (e != cudaSuccess) return e;
+  offsets_kernel<<<1, kReconThreads, 0, stream>>>(H, U, 0, L.num_chunks,
+                                                  reinterpret_cast<uint32_t*>(base + L.off_ticket),
+                                                  reinterpret_cast<uint64_t*>(base + L.off_desc),
+                                                  reinterpret_cast<uint64_t*>(base + L.off_offsets),
+                                                  reinterpret_cast<uint32_t*>(base + L.off_first), err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_offsets(const uint32_t* H, uint32_t U, uint64_t n, void* ws, const ReconLayout& L,
                            uint32_t* err, cudaStream_t stream) {
   char* base = static_cast<char*>(ws);

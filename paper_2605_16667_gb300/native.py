@@ -66,6 +66,9 @@ SIGNATURES = {
     "dialsort_read_chunk_offsets": (STATUS, [P, U32, U64, P, P]),
     "dialsort_reconstruct_noalloc": (STATUS, [P, U32, P, U64, P]),
     "dialsort_histogram_accumulate": (STATUS, [P, U32, U64, U32, P, P, SZ, P]),
+    "dialsort_radix_workspace_size": (SZ, [U64]),
+    "dialsort_radix_sort_i32": (STATUS, [P, U64, P, P, SZ, P]),
+    "dialsort_radix_sort_u32": (STATUS, [P, U64, P, P, SZ, P]),
     "dialsort_frequency": (STATUS, [P, U32, P, U64, P, P]),
     "dialsort_presence": (STATUS, [P, U32, P, U64, P, P]),
     "dialsort_range_count": (STATUS, [P, U32, P, P, U64, P, P]),
@@ -93,6 +96,8 @@ SIGNATURES = {
     "dialsort_status_string": (ctypes.c_char_p, [STATUS]),
     "dialsort_device_sm_count": (INT, []),
     "dialsort_pageable_host_access": (INT, []),
+    "dialsort_selftest_workspace_size": (SZ, []),
+    "dialsort_selftest_wait_timeout": (STATUS, [INT, P, SZ, P]),
     "dialsort_version": (ctypes.c_char_p, []),
 }
 

@@ -292,3 +292,41 @@ def test_accumulate_over_batches_equals_one_histogram():
     assert skipped == 1 and int(H2[4999]) == int(H[4999]) + 1 and int(H2[0]) == int(H[0]) + 1
     Hw, _ = oracle.accumulate(keys.astype(np.uint16), U, np.zeros(U, dtype=np.uint32))
     np.testing.assert_array_equal(Hw, np.bincount(keys, minlength=U))
+
+
+# ---- DialSort-Radix (Sec. "Full int32 range")
+
+SPECIAL = [-(2 ** 31), -(2 ** 31) + 1, -65536, -257, -256, -255, -1, 0, 1, 255, 256, 257, 65535, 65536,
+           2 ** 24, 2 ** 31 - 1]
+
+
+def test_radix_brute_force_on_special_values():
+    """Every sequence of length <= 3 over values at digit and sign boundaries, against sorted()."""
+    vals = SPECIAL[::2] + [7]
+    for length in range(4):
+        for seq in itertools.product(vals, repeat=length):
+            got = oracle.radix_sort(np.array(seq, dtype=np.int32))
+            assert got.tolist() == sorted(seq)
+    u = [0, 1, 255, 256, 2 ** 31 - 1, 2 ** 31, 2 ** 32 - 1]
+    for seq in itertools.product(u, repeat=3):
+        assert oracle.radix_sort(np.array(seq, dtype=np.uint32)).tolist() == sorted(seq)
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 1000, 100_003])
+def test_radix_equals_numpy_sort_full_int32_range(n):
+    w = gen.words(n, stream=806)
+    signed = w.astype(np.uint32).view(np.int32)
+    np.testing.assert_array_equal(oracle.radix_sort(signed), np.sort(signed))
+    np.testing.assert_array_equal(oracle.radix_sort(w.astype(np.uint32)), np.sort(w.astype(np.uint32)))
+
+
+def test_radix_special_cases():
+    vals = np.array(SPECIAL * 50, dtype=np.int32)
+    np.testing.assert_array_equal(oracle.radix_sort(vals), np.sort(vals))
+    same = np.full(1000, -7, dtype=np.int32)
+    np.testing.assert_array_equal(oracle.radix_sort(same), same)  # all equal: a fixed point
+    asc = np.sort(gen.words(5000, stream=807).astype(np.uint32).view(np.int32))
+    np.testing.assert_array_equal(oracle.radix_sort(asc), asc)  # sorted input: a fixed point
+    np.testing.assert_array_equal(oracle.radix_sort(asc[::-1].copy()), asc)  # reversed
+    small = gen.keys(20_000, 1 << 20, "zipf", stream=808).view(np.int32)  # top digits all zero
+    np.testing.assert_array_equal(oracle.radix_sort(small), np.sort(small))
