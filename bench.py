@@ -401,7 +401,7 @@ def main():
         if args.form == "batched":
             res = run_batched(ds, torch, stream)
         elif args.form == "radix":
-            res = run_radix(ds, torch, stream)
+            res = run_radix(ds, torch, stream, n=args.n)
         else:
             res = run_served(ds, torch, seconds=args.served_seconds)
         print(json.dumps({"form": args.form, **res}), flush=True)

@@ -226,6 +226,34 @@ dialsort_status_t dialsort_sort_u16(const uint16_t* keys, uint64_t n, uint32_t U
 /* Device pointer to the histogram that dialsort_sort leaves in ws. */
 uint32_t* dialsort_sort_histogram(void* ws);
 
+/* ---------------------------------------------------------------- mapped domains */
+
+/*
+ * Sorting a finite ordered domain through an order-preserving map onto
+ * [0, U) (Prop. "General Self-Indexing Principle"): every key x is counted
+ * at index phi(x) (Eq. (1) over [0, U)), then for every index i in
+ * ascending order phi_inv(i) is emitted H[i] times (Eq. (2)).  When phi
+ * preserves order the output is the keys sorted in the domain's order; the
+ * library does not check that it does.
+ *   keys, out  n raw keys of key_bytes (1, 2 or 4) each, aligned to their
+ *              width; out may equal keys.
+ *   phi, M     uint32[M] index of every raw value below M; 0xffffffff marks
+ *              a value outside the domain.  NULL: the raw value is its own
+ *              index (M ignored).  A raw key >= M, or marked outside the
+ *              domain, or whose index is >= U, is not counted and sets
+ *              DIALSORT_ERR_KEY_RANGE in the error word.
+ *   phi_inv    U raw values of key_bytes each, the key emitted for each
+ *              index.  NULL: the index itself is emitted.
+ *   ws         dialsort_sort_mapped_workspace_size(n, U) bytes, 256-byte
+ *              aligned; H is kept at its start.
+ * Examples: 8-bit pixels (key_bytes 1, phi = phi_inv = NULL, U = 256);
+ * a dictionary of sparse 32-bit codes compacted to their ranks.
+ */
+size_t dialsort_sort_mapped_workspace_size(uint64_t n, uint32_t U);
+dialsort_status_t dialsort_sort_mapped(const void* keys, uint32_t key_bytes, uint64_t n, const uint32_t* phi,
+                                       uint32_t M, const void* phi_inv, uint32_t U, void* out, void* ws,
+                                       size_t ws_bytes, void* stream);
+
 /* ---------------------------------------------------------------- DialSort-Radix */
 
 /*

@@ -18,6 +18,8 @@ Functions and the passages they follow:
   rule of Eqs. (3)-(4).
 * ``accumulate``  -- Eq. (1) without the zeroing (a stream of batches ingested
   into one H).
+* ``sort_mapped`` -- Prop. "General Self-Indexing Principle": Eq. (1) on
+  phi(key), then Eq. (2) emitting phi_inv(i).
 * ``radix_sort``  -- DialSort-Radix of Sec. "Full int32 range": four stable
   counting passes (Eq. (1) on a base-256 digit, then placement at the digit's
   cursor), least significant digit first; int32 keys sort as signed.
@@ -84,6 +86,8 @@ def _load():
             f = getattr(lib, name)
             f.restype = None
             f.argtypes = [_P, _U32, _P, _U64, _P]
+        lib.oracle_sort_mapped.restype = _U64
+        lib.oracle_sort_mapped.argtypes = [_P, _U64, _P, _U32, _P, _U32, _P, _P]
         lib.oracle_radix_sort.restype = None
         lib.oracle_radix_sort.argtypes = [_P, _U64, ctypes.c_int, _P, _P]
         lib.oracle_range_count.restype = None
@@ -144,6 +148,24 @@ def accumulate(keys: np.ndarray, U: int, H: np.ndarray) -> tuple[np.ndarray, int
         k = _c(keys, np.uint32)
         skipped = _load().oracle_accumulate_u32(k.ctypes.data, k.size, U, H.ctypes.data)
     return H, int(skipped)
+
+
+def sort_mapped(keys: np.ndarray, U: int, phi=None, phi_inv=None) -> tuple[np.ndarray, np.ndarray, int]:
+    """Prop. "General Self-Indexing Principle": count each key at phi(key), emit phi_inv(i) H[i] times.
+
+    phi: array of M indices (0xffffffff = not in the domain) or None (identity); phi_inv: U values or
+    None (identity).  Returns (out in the keys' dtype, H, number of keys not counted)."""
+    keys = np.asarray(keys)
+    k = np.ascontiguousarray(keys, dtype=np.uint32)
+    H = np.empty(U, dtype=np.uint32)
+    out = np.empty(k.size, dtype=np.uint32)
+    ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.uint32)
+    inv = None if phi_inv is None else np.ascontiguousarray(phi_inv, dtype=np.uint32)
+    skipped = _load().oracle_sort_mapped(k.ctypes.data, k.size, None if ph is None else ph.ctypes.data,
+                                         0 if ph is None else ph.size, None if inv is None else inv.ctypes.data,
+                                         U, out.ctypes.data, H.ctypes.data)
+    total = k.size - int(skipped)
+    return out[:total].astype(keys.dtype), H, int(skipped)
 
 
 def radix_sort(keys: np.ndarray) -> np.ndarray:

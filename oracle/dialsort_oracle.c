@@ -27,6 +27,9 @@
  *   oracle_accumulate_*  Eq. (1) without the zeroing: H[x] <- H[x] + 1 on an
  *                        H that already holds counts (ingesting a stream of
  *                        batches into one histogram).
+ *   oracle_sort_mapped   Prop. "General Self-Indexing Principle": count
+ *                        each key at index phi(key), then emit
+ *                        phi_inv(i) H[i] times for i = 0..U-1.
  *   oracle_radix_sort    DialSort-Radix (Sec. "Full int32 range"): four
  *                        stable counting passes over the base-256 digits,
  *                        least significant first.
@@ -238,4 +241,36 @@ void oracle_radix_sort(const uint32_t* keys, uint64_t n, int is_signed, uint32_t
     }
     src = dst;
   }
+}
+
+/*
+ * Prop. "General Self-Indexing Principle", constructive proof: step 1, for
+ * every key x compute i = phi(x) and add one to H[i]; step 2, for i = 0..U-1
+ * emit phi_inv(i) exactly H[i] times.  phi == NULL means phi(x) = x, and
+ * phi_inv == NULL means phi_inv(i) = i.  A key with x >= M (when phi is
+ * given), phi[x] == 0xffffffff, or index >= U is not in the domain: it is not
+ * counted.  Keys and output are passed widened to uint32.  H has U entries.
+ * Returns the number of keys not counted; out receives sum(H) keys.
+ */
+uint64_t oracle_sort_mapped(const uint32_t* keys, uint64_t n, const uint32_t* phi, uint32_t M,
+                            const uint32_t* phi_inv, uint32_t U, uint32_t* out, uint32_t* H) {
+  uint64_t skipped = 0;
+  for (uint64_t k = 0; k < U; ++k) H[k] = 0;
+  for (uint64_t j = 0; j < n; ++j) {
+    uint32_t i = keys[j];
+    if (phi != 0) i = keys[j] < M ? phi[keys[j]] : 0xffffffffu;
+    if (i < U)
+      H[i] = H[i] + 1;
+    else
+      skipped = skipped + 1;
+  }
+  uint64_t pos = 0;
+  for (uint64_t i = 0; i < U; ++i) {
+    const uint32_t value = phi_inv != 0 ? phi_inv[i] : (uint32_t)i;
+    for (uint32_t c = 0; c < H[i]; ++c) {
+      out[pos] = value;
+      pos = pos + 1;
+    }
+  }
+  return skipped;
 }

@@ -21,7 +21,7 @@ __all__ = [
     "DialSortError", "histogram", "reconstruct", "sort", "offsets", "plan_histogram", "stream_status",
     "sort_workspace_size", "reconstruct_workspace_size", "REGIMES", "lib", "Batch", "batched", "Server",
     "replay", "device_view", "pageable_host_access", "histogram_accumulate", "frequency", "presence",
-    "range_count", "radix_sort",
+    "range_count", "radix_sort", "sort_mapped",
 ]
 
 OK, ERR_INVALID_ARG, ERR_KEY_RANGE, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_BUSY, ERR_OVERFLOW, ERR_WORKSPACE = range(9)
@@ -215,6 +215,42 @@ def histogram_accumulate(keys: torch.Tensor, U: int, H: torch.Tensor, *, ws: tor
         keys.data_ptr(), w, keys.numel(), U, H.data_ptr(), ws.data_ptr() if ws is not None else None,
         ws.numel() if ws is not None else 0, _stream(stream)), "dialsort_histogram_accumulate")
     return H
+
+
+_W1 = (torch.uint8, torch.int8)
+
+
+def sort_mapped(keys: torch.Tensor, U: int, phi: torch.Tensor | None = None, phi_inv: torch.Tensor | None = None,
+                out: torch.Tensor | None = None, *, ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Sort through an order-preserving map onto [0, U) (Prop. "General Self-Indexing Principle").
+
+    keys: 8-, 16- or 32-bit raw keys.  phi: int32/uint32 tensor of M indices (0xffffffff = outside the
+    domain) or None (a key is its own index).  phi_inv: U raw values of the keys' width or None.
+    """
+    _reachable(keys, "keys")
+    w = 1 if keys.dtype in _W1 else _width(keys)
+    n = keys.numel()
+    if out is None:
+        out = _like(keys)
+    _reachable(out, "out")
+    if out.element_size() != w or out.numel() < n:
+        raise ValueError("out must hold n keys of the keys' width")
+    M = 0
+    if phi is not None:
+        _reachable(phi, "phi")
+        if phi.dtype not in _W4:
+            raise TypeError("phi must hold 32-bit indices")
+        M = phi.numel()
+    if phi_inv is not None:
+        _reachable(phi_inv, "phi_inv")
+        if phi_inv.element_size() != w or phi_inv.numel() < U:
+            raise ValueError("phi_inv must hold U values of the keys' width")
+    L = native.load()
+    ws = _workspace(L.dialsort_sort_mapped_workspace_size(n, U), _device(keys), ws)
+    _check(L.dialsort_sort_mapped(keys.data_ptr(), w, n, phi.data_ptr() if phi is not None else None, M,
+                                  phi_inv.data_ptr() if phi_inv is not None else None, U, out.data_ptr(),
+                                  ws.data_ptr(), ws.numel(), _stream(stream)), "dialsort_sort_mapped")
+    return out
 
 
 def radix_sort(keys: torch.Tensor, out: torch.Tensor | None = None, *, signed: bool | None = None,

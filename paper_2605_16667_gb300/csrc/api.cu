@@ -164,9 +164,54 @@ dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, ui
   return reconstruct_impl(H, U, out, key_bytes, n, base + hb, rb, st);
 }
 
+// Prop. "General Self-Indexing Principle": index = phi(key), counted by Eq. (1) over [0, U), then
+// Eq. (2) emits inv(index) for every index in order.  Single-pass ingestion regimes only (the
+// two-level path moves raw keys, not indices).
+dialsort_status_t sort_mapped_impl(const void* keys, uint32_t key_bytes, uint64_t n, const uint32_t* phi,
+                                   uint32_t M, const void* inv, uint32_t U, void* out, void* ws, size_t ws_bytes,
+                                   cudaStream_t st) {
+  if (key_bytes != 1 && key_bytes != 2 && key_bytes != 4) return DIALSORT_ERR_INVALID_ARG;
+  if (U == 0 || n >= (1ull << 32)) return DIALSORT_ERR_INVALID_ARG;
+  if (phi != nullptr && (M == 0 || (key_bytes < 4 && M > (1u << (8 * key_bytes))) || !aligned(phi, 4)))
+    return DIALSORT_ERR_INVALID_ARG;
+  if (inv != nullptr && !aligned(inv, key_bytes)) return DIALSORT_ERR_INVALID_ARG;
+  if (n > 0 && (keys == nullptr || out == nullptr || !aligned(keys, key_bytes) || !aligned(out, key_bytes)))
+    return DIALSORT_ERR_INVALID_ARG;
+  const size_t hb = sort_h_bytes(U);
+  const ReconLayout L = recon_layout(U, n);
+  if (ws == nullptr || !aligned(ws, 256) || ws_bytes < hb + L.total) return DIALSORT_ERR_WORKSPACE;
+  const DeviceInfo* dev = device_info();
+  if (!dev) return DIALSORT_ERR_CUDA;
+  const void *kp, *op, *pp, *ip;
+  dialsort_status_t s = kernel_address(n ? keys : nullptr, *dev, &kp);
+  if (s == DIALSORT_OK) s = kernel_address(n ? out : nullptr, *dev, &op);
+  if (s == DIALSORT_OK) s = kernel_address(phi, *dev, &pp);
+  if (s == DIALSORT_OK) s = kernel_address(inv, *dev, &ip);
+  if (s != DIALSORT_OK) return s;
+  HistPlan plan;
+  s = plan_histogram(n, U, key_bytes, 0, nullptr, *dev, &plan);
+  if (s != DIALSORT_OK) return s;
+  char* base = static_cast<char*>(ws);
+  uint32_t* H = reinterpret_cast<uint32_t*>(base);
+  cudaError_t e = cudaMemsetAsync(H, 0, (size_t)U * 4, st);
+  if (e == cudaSuccess && n > 0)
+    e = launch_histogram(kp, key_bytes, n, U, H, plan, dev->err, st, static_cast<const uint32_t*>(pp), M);
+  if (e == cudaSuccess) e = launch_offsets(H, U, n, base + hb, L, dev->err, st);
+  if (e == cudaSuccess) e = launch_expand(H, U, n, const_cast<void*>(op), key_bytes, base + hb, L, st, ip);
+  return from_cuda(e);
+}
+
 }  // namespace
 
 extern "C" {
+
+size_t dialsort_sort_mapped_workspace_size(uint64_t n, uint32_t U) { return sort_h_bytes(U) + recon_layout(U, n).total; }
+
+dialsort_status_t dialsort_sort_mapped(const void* keys, uint32_t key_bytes, uint64_t n, const uint32_t* phi,
+                                       uint32_t M, const void* phi_inv, uint32_t U, void* out, void* ws,
+                                       size_t ws_bytes, void* stream) {
+  return sort_mapped_impl(keys, key_bytes, n, phi, M, phi_inv, U, out, ws, ws_bytes, as_stream(stream));
+}
 
 size_t dialsort_selftest_workspace_size(void) {
   return std::max(offsets_selftest_bytes(), radix_selftest_bytes());

@@ -30,7 +30,7 @@ namespace dialsort {
 template <typename KeyT, int MODE>
 __global__ void __launch_bounds__(1024) hist_kernel(const KeyT* __restrict__ keys, uint64_t n, uint32_t U,
                                                     uint32_t* __restrict__ H, uint32_t* err, uint32_t replicas,
-                                                    uint32_t words_per_copy, uint32_t crn_mode) {
+                                                    uint32_t words_per_copy, uint32_t crn_mode, KeyMap map) {
   extern __shared__ __align__(16) uint32_t sh[];
   const uint32_t warp = threadIdx.x >> 5;
   // the global sink keeps bins [0, S) in shared memory (S = words_per_copy, capped at U)
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(1024) hist_kernel(const KeyT* __restrict__ key
   const Sink<MODE> s{sh + (warp % replicas) * words_per_copy, H, U, S};
   bool bad = false;
   ingest_span<KeyT, MODE>(keys, n, U, s, (uint64_t)blockIdx.x * blockDim.x + warp * 32u,
-                          (uint64_t)gridDim.x * blockDim.x, blockIdx.x == gridDim.x - 1, crn_mode, bad);
+                          (uint64_t)gridDim.x * blockDim.x, blockIdx.x == gridDim.x - 1, crn_mode, bad, map);
   if (bad) raise_error(err, ERRBIT_KEY_RANGE);
   __syncthreads();
   flush_smem<MODE>(sh, replicas, words_per_copy, MODE == MODE_GLOBAL ? S : U, H, false);
@@ -63,10 +63,17 @@ const void* pick_kernel(uint32_t key_bytes, int mode) {
       default: return kernel_ptr<uint32_t, MODE_GLOBAL>();
     }
   }
+  if (key_bytes == 2) {
+    switch (mode) {
+      case MODE_SMEM32: return kernel_ptr<uint16_t, MODE_SMEM32>();
+      case MODE_SMEM16: return kernel_ptr<uint16_t, MODE_SMEM16>();
+      default: return kernel_ptr<uint16_t, MODE_GLOBAL>();
+    }
+  }
   switch (mode) {
-    case MODE_SMEM32: return kernel_ptr<uint16_t, MODE_SMEM32>();
-    case MODE_SMEM16: return kernel_ptr<uint16_t, MODE_SMEM16>();
-    default: return kernel_ptr<uint16_t, MODE_GLOBAL>();
+    case MODE_SMEM32: return kernel_ptr<uint8_t, MODE_SMEM32>();
+    case MODE_SMEM16: return kernel_ptr<uint8_t, MODE_SMEM16>();
+    default: return kernel_ptr<uint8_t, MODE_GLOBAL>();
   }
 }
 
@@ -81,14 +88,16 @@ int mode_of(uint32_t regime) {
 }  // namespace
 
 cudaError_t launch_histogram(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
-                             const HistPlan& plan, uint32_t* err, cudaStream_t stream) {
+                             const HistPlan& plan, uint32_t* err, cudaStream_t stream, const uint32_t* phi,
+                             uint32_t M) {
   const void* fn = pick_kernel(key_bytes, mode_of(plan.regime));
   if (plan.smem_bytes > 48u * 1024u) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes);
     if (e != cudaSuccess) return e;
   }
   uint32_t replicas = plan.replicas, wpc = plan.words_per_copy, crn = plan.crn;
-  void* args[] = {const_cast<void**>(&keys), &n, &U, &H, &err, &replicas, &wpc, &crn};
+  KeyMap map{phi, M};
+  void* args[] = {const_cast<void**>(&keys), &n, &U, &H, &err, &replicas, &wpc, &crn, &map};
   return cudaLaunchKernel(fn, dim3(plan.blocks), dim3(plan.threads), args, plan.smem_bytes, stream);
 }
 

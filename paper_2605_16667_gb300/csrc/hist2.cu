@@ -332,12 +332,21 @@ constexpr uint32_t kP2Warps = kP2Threads / 32;
 constexpr uint32_t kP2Unroll = 4;
 constexpr uint32_t kP2LongSegment = 16;  // mean chunks per tile from which a warp takes one tile at a time
 
+// Count one chunk per lane (all 32 lanes call this together).  A chunk of
+// eight equal low parts (a hot or repeated key) is one item (key, 8) -- the
+// CRN lane's local accumulation; when some lanes hold such items, equal ones
+// are merged across the warp (match.any, the CRN's equality merge) and one
+// lane adds their sum, so sorted or repeated keys do not pile 32 lanes onto
+// one shared-memory address.
 template <int MODE>
-__device__ __forceinline__ void count_chunk(const Sink<MODE>& s, const uint4& q, uint32_t vm) {
+__device__ __forceinline__ void count_chunk(const Sink<MODE>& s, const uint4& q, uint32_t vm, uint32_t lane) {
   const uint32_t k[8] = {q.x & 0xffffu, q.x >> 16, q.y & 0xffffu, q.y >> 16,
                          q.z & 0xffffu, q.z >> 16, q.w & 0xffffu, q.w >> 16};
-  if (vm == 0xffu && q.x == q.y && q.x == q.z && q.x == q.w && k[0] == k[1]) {
-    s.add(k[0], 8u);  // eight equal low parts (a hot or repeated key): one add
+  const bool same8 = vm == 0xffu && q.x == q.y && q.x == q.z && q.x == q.w && k[0] == k[1];
+  const uint32_t m = __ballot_sync(0xffffffffu, same8);
+  if (same8) {
+    const uint32_t peers = __match_any_sync(m, k[0]);
+    if ((peers & ((1u << lane) - 1u)) == 0) s.add(k[0], 8u * (uint32_t)__popc(peers));
   } else {
 #pragma unroll
     for (uint32_t i = 0; i < 8; ++i)
@@ -404,7 +413,7 @@ __global__ void __launch_bounds__(kP2Threads, 2) bucket_kernel(const uint16_t* _
           }
         }
 #pragma unroll
-        for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u]);
+        for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u], lane);
       }
     }
   } else {
@@ -451,7 +460,7 @@ __global__ void __launch_bounds__(kP2Threads, 2) bucket_kernel(const uint16_t* _
           }
         }
 #pragma unroll
-        for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u]);
+        for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u], lane);
       }
     }
   }

@@ -71,6 +71,19 @@ struct Sink<MODE_GLOBAL> {
   }
 };
 
+// Optional map from a raw key to its index (Prop. "General Self-Indexing
+// Principle": phi, an order-preserving map of the key domain onto [0, U)).
+// phi == nullptr: the key is its own index.  A raw key x >= M, or one whose
+// phi[x] is 0xffffffff (not in the domain), maps to 0xffffffff, which the
+// range check then reports like any key >= U.
+struct KeyMap {
+  const uint32_t* phi;
+  uint32_t M;
+  __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
+    return phi == nullptr ? x : (x < M ? __ldg(phi + x) : 0xffffffffu);
+  }
+};
+
 template <typename KeyT>
 struct Vec;
 template <>
@@ -81,6 +94,20 @@ struct Vec<uint32_t> {
     k[1] = q.y;
     k[2] = q.z;
     k[3] = q.w;
+  }
+};
+template <>
+struct Vec<uint8_t> {
+  static constexpr int K = 16;
+  __device__ __forceinline__ static void unpack(const uint4& q, uint32_t (&k)[16]) {
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      k[4 * i] = w[i] & 0xffu;
+      k[4 * i + 1] = (w[i] >> 8) & 0xffu;
+      k[4 * i + 2] = (w[i] >> 16) & 0xffu;
+      k[4 * i + 3] = w[i] >> 24;
+    }
   }
 };
 template <>
@@ -189,7 +216,7 @@ __device__ __forceinline__ void ingest(const uint32_t (&k)[KPV], bool valid, con
 template <typename KeyT, int MODE>
 __device__ __forceinline__ void ingest_span(const KeyT* __restrict__ keys, uint64_t n, uint32_t U,
                                             const Sink<MODE>& s, uint64_t first, uint64_t stride, bool do_scalars,
-                                            uint32_t crn_mode, bool& bad) {
+                                            uint32_t crn_mode, bool& bad, const KeyMap map = KeyMap{nullptr, 0u}) {
   constexpr int KPV = Vec<KeyT>::K;
   constexpr int UNR = 4;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -212,6 +239,10 @@ __device__ __forceinline__ void ingest_span(const KeyT* __restrict__ keys, uint6
     for (int u = 0; u < UNR; ++u) {
       uint32_t k[KPV];
       Vec<KeyT>::unpack(q[u], k);
+      if (map.phi != nullptr) {
+#pragma unroll
+        for (int j = 0; j < KPV; ++j) k[j] = map(k[j]);
+      }
       ingest<KPV, MODE>(k, v0 + u * stride + lane < nvec, s, U, bad, crn_mode, score);
     }
   }
@@ -219,7 +250,7 @@ __device__ __forceinline__ void ingest_span(const KeyT* __restrict__ keys, uint6
     for (uint64_t i0 = warp * 32u; i0 < nscalar; i0 += blockDim.x) {
       const uint64_t i = i0 + lane;
       uint32_t k[1] = {0u};
-      if (i < nscalar) k[0] = keys[i < head ? i : tail0 + (i - head)];
+      if (i < nscalar) k[0] = map(keys[i < head ? i : tail0 + (i - head)]);
       ingest<1, MODE>(k, i < nscalar, s, U, bad, crn_mode, score);
     }
   }

@@ -44,8 +44,10 @@ dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uin
                                  const dialsort_hist_config_t* cfg, const DeviceInfo& dev, HistPlan* plan);
 
 // Step 1 kernels (H must already be zero).  hist.cu
+// phi (optional): index = phi[key] for keys < M (see KeyMap); key_bytes 1, 2 or 4.
 cudaError_t launch_histogram(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
-                             const HistPlan& plan, uint32_t* err, cudaStream_t stream);
+                             const HistPlan& plan, uint32_t* err, cudaStream_t stream,
+                             const uint32_t* phi = nullptr, uint32_t M = 0);
 
 // Two-level ingestion for large universes.  hist2.cu
 struct TwoLevelLayout {
@@ -83,8 +85,9 @@ ReconLayout recon_layout(uint32_t U, uint64_t n);
 
 cudaError_t launch_offsets(const uint32_t* H, uint32_t U, uint64_t n, void* ws, const ReconLayout& L,
                            uint32_t* err, cudaStream_t stream);
+// inv (optional): index k is written as inv[k] (an array of out_bytes-wide values); out_bytes 1, 2 or 4.
 cudaError_t launch_expand(const uint32_t* H, uint32_t U, uint64_t n, void* out, uint32_t out_bytes, void* ws,
-                          const ReconLayout& L, cudaStream_t stream);
+                          const ReconLayout& L, cudaStream_t stream, const void* inv = nullptr);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

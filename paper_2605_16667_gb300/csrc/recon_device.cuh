@@ -165,7 +165,7 @@ __device__ __forceinline__ void note_run(ExpandSmem& sm, uint32_t s, uint32_t e,
   if (e - s >= kLongRun) {
     const uint32_t i = atomicAdd(&sm.nlong, 1u);
     if (i < 4) sm.longs[i] = make_uint2(s | (e << 16), key);
-  } else {
+  } else if (*reinterpret_cast<volatile uint32_t*>(&sm.nruns) <= kPaintRuns) {  // past the cap: stop counting
     const uint32_t i = atomicAdd(&sm.nruns, 1u);
     if (i < kPaintRuns) sm.runs[i] = make_uint2(s | (e << 16), key);
   }
@@ -187,9 +187,12 @@ __device__ __forceinline__ void paint_run(OutT* __restrict__ dst, uint32_t s, ui
   uint4 v;
   if (sizeof(OutT) == 4) {
     v = make_uint4(key, key, key, key);
-  } else {
+  } else if (sizeof(OutT) == 2) {
     const uint32_t k2 = (key & 0xffffu) | (key << 16);
     v = make_uint4(k2, k2, k2, k2);
+  } else {
+    const uint32_t k4 = (key & 0xffu) * 0x01010101u;
+    v = make_uint4(k4, k4, k4, k4);
   }
   uint4* d4 = reinterpret_cast<uint4*>(dst + a);
   for (uint32_t q = lane; q < (b - a) / kPer; q += lanes) d4[q] = v;
@@ -199,11 +202,14 @@ __device__ __forceinline__ void paint_run(OutT* __restrict__ dst, uint32_t s, ui
 // Output tile `tile` (keys [tile * 8192, ...)) of the projection.  Marks the
 // slot where each run starts (slot 0 gets the run covering the tile's first
 // key), fills forward ("latest mark wins"), and stores with 128-bit stores.
+// With inv, index k is written as inv[k] (the inverse map of Prop. "General
+// Self-Indexing Principle"); without it, as k.
 template <typename OutT>
 __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint32_t U, uint64_t n_cap,
                                             uint64_t num_chunks, const uint64_t* __restrict__ O,
                                             const uint32_t* __restrict__ first_chunk, OutT* __restrict__ out,
-                                            int out_aligned, uint64_t tile, ExpandSmem& sm) {
+                                            int out_aligned, uint64_t tile, ExpandSmem& sm,
+                                            const OutT* __restrict__ inv = nullptr) {
   uint32_t* M = sm.M;
   uint32_t* red32 = sm.red32;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
@@ -305,11 +311,13 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
   if (nruns <= kPaintRuns) {  // few runs: paint each with its key
     for (uint32_t r = warp; r < nruns; r += kReconThreads / 32) {
       const uint2 run = sm.runs[r];
-      paint_run<OutT>(dst, run.x & 0xffffu, run.x >> 16, run.y, out_aligned, lane, 32u);
+      const uint32_t key = inv != nullptr ? (uint32_t)inv[run.y] : run.y;
+      paint_run<OutT>(dst, run.x & 0xffffu, run.x >> 16, key, out_aligned, lane, 32u);
     }
     for (uint32_t r = 0; r < nlong && r < 4; ++r) {
       const uint2 run = sm.longs[r];
-      paint_run<OutT>(dst, run.x & 0xffffu, run.x >> 16, run.y, out_aligned, tid, kReconThreads);
+      const uint32_t key = inv != nullptr ? (uint32_t)inv[run.y] : run.y;
+      paint_run<OutT>(dst, run.x & 0xffffu, run.x >> 16, key, out_aligned, tid, kReconThreads);
     }
     __syncthreads();  // sm is reused by the caller's next item
     return;
@@ -358,11 +366,15 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
     const uint32_t m3 = q.w ? q.w : m2;
     q = make_uint4(m0 - 1u, m1 - 1u, m2 - 1u, m3 - 1u);  // marks hold key + 1
     if (slot >= len) continue;
+    if (inv != nullptr) q = make_uint4(inv[q.x], inv[q.y], inv[q.z], inv[q.w]);
     if (slot + 4 <= len && out_aligned) {
       if (sizeof(OutT) == 4) {
         *reinterpret_cast<uint4*>(dst + slot) = q;
-      } else {
+      } else if (sizeof(OutT) == 2) {
         *reinterpret_cast<uint2*>(dst + slot) = make_uint2(q.x | (q.y << 16), q.z | (q.w << 16));
+      } else {
+        *reinterpret_cast<uint32_t*>(dst + slot) =
+            (q.x & 0xffu) | ((q.y & 0xffu) << 8) | ((q.z & 0xffu) << 16) | (q.w << 24);
       }
     } else {
       dst[slot] = (OutT)q.x;

@@ -46,9 +46,10 @@ __global__ void __launch_bounds__(kReconThreads, 6) expand_kernel(const uint32_t
                                                                   uint64_t n_cap, uint64_t num_chunks,
                                                                   const uint64_t* __restrict__ O,
                                                                   const uint32_t* __restrict__ first_chunk,
-                                                                  OutT* __restrict__ out, int out_aligned) {
+                                                                  OutT* __restrict__ out, int out_aligned,
+                                                                  const OutT* __restrict__ inv) {
   __shared__ __align__(16) ExpandSmem sm;
-  expand_tile<OutT>(H, U, n_cap, num_chunks, O, first_chunk, out, out_aligned, blockIdx.x, sm);
+  expand_tile<OutT>(H, U, n_cap, num_chunks, O, first_chunk, out, out_aligned, blockIdx.x, sm, inv);
 }
 
 }  // namespace
@@ -105,23 +106,27 @@ cudaError_t launch_offsets(const uint32_t* H, uint32_t U, uint64_t n, void* ws, 
 }
 
 cudaError_t launch_expand(const uint32_t* H, uint32_t U, uint64_t n, void* out, uint32_t out_bytes, void* ws,
-                          const ReconLayout& L, cudaStream_t stream) {
+                          const ReconLayout& L, cudaStream_t stream, const void* inv) {
   if (L.num_tiles == 0) return cudaSuccess;
   char* base = static_cast<char*>(ws);
   const uint64_t* O = reinterpret_cast<const uint64_t*>(base + L.off_offsets);
   const uint32_t* first = reinterpret_cast<const uint32_t*>(base + L.off_first);
   const int aligned = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
   // 6 CTAs of 32 KB per SM need the large shared-memory carve-out
-  const void* fn = out_bytes == 4 ? reinterpret_cast<const void*>(&expand_kernel<uint32_t>)
-                                  : reinterpret_cast<const void*>(&expand_kernel<uint16_t>);
+  const void* fn = out_bytes == 4   ? reinterpret_cast<const void*>(&expand_kernel<uint32_t>)
+                   : out_bytes == 2 ? reinterpret_cast<const void*>(&expand_kernel<uint16_t>)
+                                    : reinterpret_cast<const void*>(&expand_kernel<uint8_t>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   if (out_bytes == 4)
     expand_kernel<uint32_t><<<(unsigned)L.num_tiles, kReconThreads, 0, stream>>>(
-        H, U, n, L.num_chunks, O, first, static_cast<uint32_t*>(out), aligned);
-  else
+        H, U, n, L.num_chunks, O, first, static_cast<uint32_t*>(out), aligned, static_cast<const uint32_t*>(inv));
+  else if (out_bytes == 2)
     expand_kernel<uint16_t><<<(unsigned)L.num_tiles, kReconThreads, 0, stream>>>(
-        H, U, n, L.num_chunks, O, first, static_cast<uint16_t*>(out), aligned);
+        H, U, n, L.num_chunks, O, first, static_cast<uint16_t*>(out), aligned, static_cast<const uint16_t*>(inv));
+  else
+    expand_kernel<uint8_t><<<(unsigned)L.num_tiles, kReconThreads, 0, stream>>>(
+        H, U, n, L.num_chunks, O, first, static_cast<uint8_t*>(out), aligned, static_cast<const uint8_t*>(inv));
   return cudaGetLastError();
 }
 

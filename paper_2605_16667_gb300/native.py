@@ -66,6 +66,8 @@ SIGNATURES = {
     "dialsort_read_chunk_offsets": (STATUS, [P, U32, U64, P, P]),
     "dialsort_reconstruct_noalloc": (STATUS, [P, U32, P, U64, P]),
     "dialsort_histogram_accumulate": (STATUS, [P, U32, U64, U32, P, P, SZ, P]),
+    "dialsort_sort_mapped_workspace_size": (SZ, [U64, U32]),
+    "dialsort_sort_mapped": (STATUS, [P, U32, U64, P, U32, P, U32, P, P, SZ, P]),
     "dialsort_radix_workspace_size": (SZ, [U64]),
     "dialsort_radix_sort_i32": (STATUS, [P, U64, P, P, SZ, P]),
     "dialsort_radix_sort_u32": (STATUS, [P, U64, P, P, SZ, P]),

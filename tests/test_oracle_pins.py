@@ -330,3 +330,52 @@ def test_radix_special_cases():
     np.testing.assert_array_equal(oracle.radix_sort(asc[::-1].copy()), asc)  # reversed
     small = gen.keys(20_000, 1 << 20, "zipf", stream=808).view(np.int32)  # top digits all zero
     np.testing.assert_array_equal(oracle.radix_sort(small), np.sort(small))
+
+
+# ---- mapped domains (Prop. "General Self-Indexing Principle")
+
+def test_mapped_identity_examples_of_the_proposition():
+    """The proposition's own domains with phi = identity: characters (code points), grayscale
+    pixels (U = 256), MIDI notes (U = 128), calendar days (U = 366)."""
+    text = b"DIALSORT SORTS WITHOUT COMPARISONS"
+    out, H, skipped = oracle.sort_mapped(np.frombuffer(text, dtype=np.uint8), 128)
+    assert skipped == 0 and bytes(out) == bytes(sorted(text))
+    pixels = gen.keys(50_000, 256, "zipf", stream=809).astype(np.uint8)
+    out, H, _ = oracle.sort_mapped(pixels, 256)
+    np.testing.assert_array_equal(out, np.sort(pixels))
+    np.testing.assert_array_equal(H, np.bincount(pixels, minlength=256))
+    notes = gen.keys(3000, 128, "uniform", stream=810).astype(np.uint8)
+    np.testing.assert_array_equal(oracle.sort_mapped(notes, 128)[0], np.sort(notes))
+    days = gen.keys(4000, 366, "uniform", stream=811).astype(np.uint16)
+    np.testing.assert_array_equal(oracle.sort_mapped(days, 366)[0], np.sort(days))
+
+
+def test_mapped_sparse_domain_through_rank_maps():
+    """S = 500 distinct 32-bit values; phi = rank in S, phi_inv = S in order: sorting through the
+    index space gives the library sort of the keys."""
+    S = np.unique(gen.keys(600, 1 << 24, "uniform", stream=812))[:500]
+    M = int(S.max()) + 1
+    phi = np.full(M, 0xFFFFFFFF, dtype=np.uint32)
+    phi[S] = np.arange(S.size, dtype=np.uint32)
+    keys = S[gen.keys(20_000, S.size, "zipf", stream=813)]
+    out, H, skipped = oracle.sort_mapped(keys, S.size, phi, S)
+    assert skipped == 0
+    np.testing.assert_array_equal(out, np.sort(keys))
+    bad = keys.copy()
+    gap = int(np.setdiff1d(np.arange(M, dtype=np.uint32), S)[0])  # a raw value below M outside S
+    bad[:3] = [M + 5, gap, M + 7]
+    out2, _, skipped2 = oracle.sort_mapped(bad, S.size, phi, S)
+    assert skipped2 == 3 and out2.size == keys.size - 3
+
+
+def test_mapped_follows_phi_order_not_key_order():
+    """A phi that reverses the domain emits the keys in descending raw order."""
+    U = 1000
+    phi = (U - 1 - np.arange(U)).astype(np.uint32)
+    keys = gen.keys(5000, U, "uniform", stream=814)
+    out, _, _ = oracle.sort_mapped(keys, U, phi, phi)  # phi is its own inverse
+    np.testing.assert_array_equal(out, np.sort(keys)[::-1])
+    tiny = [3, 1, 2, 1]
+    got = oracle.sort_mapped(np.array(tiny, dtype=np.uint32), 4, np.array([3, 2, 1, 0], dtype=np.uint32),
+                             np.array([3, 2, 1, 0], dtype=np.uint32))[0].tolist()
+    assert got == sorted(tiny, key=lambda x: 3 - x)
