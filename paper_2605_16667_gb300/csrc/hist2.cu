@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t
                                                                    uint32_t U, uint32_t L, uint32_t B,
                                                                    uint64_t num_tiles, uint16_t* __restrict__ low,
                                                                    uint16_t* __restrict__ toff,
+                                                                   uint16_t* __restrict__ tcnt,
                                                                    uint32_t* __restrict__ btot, uint32_t* err) {
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* cnt = sm;                          // [B][kCntStride]: counts, then bases
@@ -187,7 +188,11 @@ __global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t
     for (uint32_t b = tid; b <= B; b += kP1Threads) {
       const uint32_t start = b < B ? cnt[b * kCntStride] : tile_valid;
       trow[b] = (uint16_t)start;
-      if (b < B) bacc[b] += (b + 1 < B ? cnt[(b + 1) * kCntStride] : tile_valid) - start;
+      if (b < B) {
+        const uint32_t c = (b + 1 < B ? cnt[(b + 1) * kCntStride] : tile_valid) - start;
+        bacc[b] += c;
+        tcnt[(uint64_t)b * num_tiles + t] = (uint16_t)c;  // bucket-major copy for the split
+      }
     }
     // every key to its slot: base of its (bucket, warp) + its rank
     if (vm == 0xffffu) {
@@ -262,9 +267,10 @@ __global__ void __launch_bounds__(1024) plan_kernel(const uint32_t* __restrict__
 }
 
 // One CTA per bucket: cut the bucket into parts of about item_keys keys along
-// the tiles, by a scan of the bucket's per-tile counts (a tile is never
-// split; parts differ from item_keys by less than a tile).
-__global__ void __launch_bounds__(1024) split_kernel(const uint16_t* __restrict__ toff, uint32_t B,
+// the tiles, by a scan of the bucket's per-tile counts (pass 1 keeps them
+// bucket-major for this read; a tile is never split; parts differ from
+// item_keys by less than a tile).
+__global__ void __launch_bounds__(1024) split_kernel(const uint16_t* __restrict__ tcnt, uint32_t B,
                                                      uint64_t num_tiles, uint64_t item_keys,
                                                      const uint32_t* __restrict__ pbase, Item* __restrict__ items,
                                                      uint64_t max_items) {
@@ -276,11 +282,7 @@ __global__ void __launch_bounds__(1024) split_kernel(const uint16_t* __restrict_
   uint64_t running = 0;
   for (uint64_t c = 0; c < num_tiles; c += 1024) {
     const uint64_t t = c + tid;
-    uint32_t cnt = 0;
-    if (t < num_tiles) {
-      const uint16_t* row = toff + t * (uint64_t)(B + 1);
-      cnt = (uint32_t)row[b + 1] - (uint32_t)row[b];
-    }
+    const uint32_t cnt = t < num_tiles ? (uint32_t)tcnt[(uint64_t)b * num_tiles + t] : 0u;
     uint32_t x = cnt;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -399,12 +401,13 @@ __global__ void __launch_bounds__(kP2Threads, 2) bucket_kernel(const uint16_t* _
       if (a1 <= a0) continue;
       const uint32_t c_end = (a1 + 7u) >> 3;
       const uint4* tile4 = low4 + t * (uint64_t)(kP1Tile / 8);
-      for (uint32_t c0 = (a0 >> 3) + lane; c0 < c_end; c0 += 32u * kP2Unroll) {
+      // the loop bound is warp-uniform: count_chunk is a warp collective
+      for (uint32_t c0 = a0 >> 3; c0 < c_end; c0 += 32u * kP2Unroll) {
         uint4 q[kP2Unroll];
         uint32_t vm[kP2Unroll];
 #pragma unroll
         for (uint32_t u = 0; u < kP2Unroll; ++u) {
-          const uint32_t c = c0 + 32u * u;
+          const uint32_t c = c0 + 32u * u + lane;
           vm[u] = 0;
           q[u] = make_uint4(0u, 0u, 0u, 0u);
           if (c < c_end) {
@@ -486,6 +489,8 @@ TwoLevelLayout two_level_layout(uint64_t n, uint32_t U) {
   o = align_up(o + 2 * T.num_tiles * kP1Tile, 256);
   T.off_toff = o;
   o = align_up(o + 2 * T.num_tiles * (T.B + 1), 256);
+  T.off_tcnt = o;
+  o = align_up(o + 2 * T.num_tiles * T.B, 256);
   T.off_btot = o;
   o = align_up(o + 4 * (size_t)T.B, 256);
   T.off_items = o;
@@ -517,6 +522,7 @@ cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   char* base = static_cast<char*>(ws);
   uint16_t* low = reinterpret_cast<uint16_t*>(base + T.off_low);
   uint16_t* toff = reinterpret_cast<uint16_t*>(base + T.off_toff);
+  uint16_t* tcnt = reinterpret_cast<uint16_t*>(base + T.off_tcnt);
   uint32_t* btot = reinterpret_cast<uint32_t*>(base + T.off_btot);
   Item* items = reinterpret_cast<Item*>(base + T.off_items);
   uint32_t* nitems = reinterpret_cast<uint32_t*>(base + T.off_nitems);
@@ -531,12 +537,12 @@ cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   if (e != cudaSuccess) return e;
   const uint64_t grid1 = std::min<uint64_t>(T.num_tiles, (uint64_t)dev.sms * std::max(per_sm, 1));
   partition_kernel<<<(unsigned)grid1, kP1Threads, p1_smem, stream>>>(keys, n, U, T.L, T.B, T.num_tiles, low, toff,
-                                                                    btot, err);
+                                                                    tcnt, btot, err);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   uint32_t* pbase = reinterpret_cast<uint32_t*>(base + T.off_pbase);
   plan_kernel<<<1, 1024, 0, stream>>>(btot, T.B, T.item_keys, pbase, nitems);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  split_kernel<<<T.B, 1024, 0, stream>>>(toff, T.B, T.num_tiles, T.item_keys, pbase, items, T.max_items);
+  split_kernel<<<T.B, 1024, 0, stream>>>(tcnt, T.B, T.num_tiles, T.item_keys, pbase, items, T.max_items);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (!accumulate) e = cudaMemsetAsync(H, 0, (size_t)U * 4, stream);
   if (e != cudaSuccess) return e;

@@ -53,7 +53,8 @@ cudaError_t launch_histogram(const void* keys, uint32_t key_bytes, uint64_t n, u
 struct TwoLevelLayout {
   uint32_t L = 0, B = 0;          // low bits per key; buckets = ceil(U / 2^L)
   uint64_t num_tiles = 0, item_keys = 0, max_items = 0;
-  size_t off_low = 0, off_toff = 0, off_btot = 0, off_items = 0, off_nitems = 0, off_pbase = 0, total = 0;
+  size_t off_low = 0, off_toff = 0, off_tcnt = 0, off_btot = 0, off_items = 0, off_nitems = 0, off_pbase = 0;
+  size_t total = 0;
   bool p2_smem32 = true;          // pass-2 histograms in 32-bit counters (else packed 16-bit)
   uint32_t words_per_copy = 0;
 };
