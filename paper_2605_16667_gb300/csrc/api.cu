@@ -48,8 +48,9 @@ const DeviceInfo* device_info() {
   return g_dev[dev].device == dev ? &g_dev[dev] : nullptr;
 }
 
-dialsort_status_t kernel_address(const void* p, const DeviceInfo& dev, const void** q) {
+dialsort_status_t kernel_address(const void* p, const DeviceInfo& dev, const void** q, bool* in_host) {
   *q = p;
+  if (in_host) *in_host = false;
   if (p == nullptr) return DIALSORT_OK;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -64,8 +65,10 @@ dialsort_status_t kernel_address(const void* p, const DeviceInfo& dev, const voi
     case cudaMemoryTypeHost:  // page-locked: the mapped address (equal to p under unified addressing)
       if (a.devicePointer == nullptr) return DIALSORT_ERR_INVALID_ARG;
       *q = a.devicePointer;
+      if (in_host) *in_host = true;
       return DIALSORT_OK;
     default:  // pageable host memory
+      if (in_host) *in_host = true;
       return dev.pageable ? DIALSORT_OK : DIALSORT_ERR_INVALID_ARG;
   }
 }
@@ -100,7 +103,8 @@ dialsort_status_t histogram_impl(const void* keys, uint32_t key_bytes, uint64_t 
   if (!dev) return DIALSORT_ERR_CUDA;
   const void* kp;
   const void* hp;
-  if ((s = kernel_address(n ? keys : nullptr, *dev, &kp)) != DIALSORT_OK) return s;
+  bool keys_in_host = false;
+  if ((s = kernel_address(n ? keys : nullptr, *dev, &kp, &keys_in_host)) != DIALSORT_OK) return s;
   if ((s = kernel_address(H, *dev, &hp)) != DIALSORT_OK) return s;
   keys = kp;
   H = static_cast<uint32_t*>(const_cast<void*>(hp));
@@ -111,7 +115,8 @@ dialsort_status_t histogram_impl(const void* keys, uint32_t key_bytes, uint64_t 
   const bool forced = plan.regime == DIALSORT_REGIME_TWO_LEVEL;
   const bool auto_large = (cfg == nullptr || cfg->regime == DIALSORT_REGIME_AUTO) &&
                           (plan.regime == DIALSORT_REGIME_GLOBAL_CRN || plan.regime == DIALSORT_REGIME_GLOBAL);
-  if ((forced || auto_large) && two_level_fits(n, U, key_bytes, keys)) {
+  // the two-level pass 1 moves keys with bulk (TMA) copies from device memory
+  if ((forced || auto_large) && !keys_in_host && two_level_fits(n, U, key_bytes, keys)) {
     const TwoLevelLayout T = two_level_layout(n, U);
     if (ws != nullptr && ws_bytes >= T.total)
       return from_cuda(launch_two_level(static_cast<const uint32_t*>(keys), n, U, H, ws, T, plan.crn, *dev,

@@ -43,10 +43,15 @@ struct Item {
 // scan while one warp's buckets spread over all banks for the atomics.
 constexpr uint32_t kCntStride = kP1Warps + 1;
 
-// shared-memory words before the staging buffer: counters, bucket totals, scan scratch; a multiple of 4
-__host__ __device__ __forceinline__ uint32_t p1_stage_words(uint32_t B) {
-  return (B * kCntStride + B + 32 + 3) & ~3u;
+// Pass-1 shared memory, in 32-bit words: the tile's keys (filled by a bulk
+// copy), the staged low parts, the counters, the bucket totals, scan scratch
+// and the copy's mbarrier.
+__host__ __device__ __forceinline__ uint32_t p1_words(uint32_t B) {
+  return kP1Tile + kP1Tile / 2 + B * kCntStride + B + 32 + 2;
 }
+
+// Polls of a bulk copy's mbarrier before it is given up (each poll waits a while in hardware).
+constexpr uint32_t kCopyPolls = 1u << 16;
 
 // ------------------------------------------------------------------ pass 1
 // Thread tid owns keys [16 tid, 16 tid + 16) of the tile.  Each key takes its
@@ -55,46 +60,66 @@ __host__ __device__ __forceinline__ uint32_t p1_stage_words(uint32_t B) {
 // the key's slot in the tile's bucket-grouped order.  Runs of one bucket
 // within a thread (skew, sorted input, repeated keys) take one atomic per
 // run; the warp decides together whether to look for runs.
-__global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t* __restrict__ keys, uint64_t n,
+//
+// Data movement is by bulk (1-D TMA) copies: one thread starts the copy of
+// the CTA's next 32 KB tile into shared memory as soon as the current tile's
+// keys have been read for the last time, so the load overlaps the scan and
+// the write-out; the grouped low parts leave by a bulk store.  Keys never
+// stay in registers across a barrier, which leaves room for 3 CTAs per SM.
+__global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t* __restrict__ keys, uint64_t n,
                                                                    uint32_t U, uint32_t L, uint32_t B,
                                                                    uint64_t num_tiles, uint16_t* __restrict__ low,
                                                                    uint16_t* __restrict__ toff,
                                                                    uint16_t* __restrict__ tcnt,
                                                                    uint32_t* __restrict__ btot, uint32_t* err) {
-  extern __shared__ __align__(16) uint32_t sm[];
-  uint32_t* cnt = sm;                          // [B][kCntStride]: counts, then bases
-  uint32_t* bacc = cnt + B * kCntStride;       // [B]: this CTA's bucket totals over its tiles
-  uint32_t* red = bacc + B;                    // block scan scratch (32 words)
-  // [kP1Tile] low parts of one tile, read as uint4: starts on a 16-byte boundary
-  uint16_t* stage = reinterpret_cast<uint16_t*>(sm + p1_stage_words(B));
+  extern __shared__ __align__(128) uint32_t sm[];
+  uint32_t* kbuf = sm;                                           // [8192] keys of the tile
+  uint16_t* stage = reinterpret_cast<uint16_t*>(sm + kP1Tile);   // [8192] grouped low parts
+  uint32_t* cnt = sm + kP1Tile + kP1Tile / 2;                    // [B][kCntStride]: counts, then bases
+  uint32_t* bacc = cnt + B * kCntStride;                         // [B]: this CTA's bucket totals
+  uint32_t* red = bacc + B;                                      // [32] scan scratch; red[31]: stop flag
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + 32);         // the key copy's mbarrier
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t lowmask = (1u << L) - 1u;
   const uint32_t ncnt = B * kCntStride;
+  const uint64_t full_tiles = n / kP1Tile;  // tiles loaded by a bulk copy; the ragged last one by plain loads
   bool bad = false;
+  uint32_t parity = 0;
 
   for (uint32_t b = tid; b < B; b += kP1Threads) bacc[b] = 0;
+  if (tid == 0) {
+    red[31] = 0;
+    mbar_init(bar, 1);
+    if (blockIdx.x < full_tiles)
+      bulk_load(kbuf, keys + (uint64_t)blockIdx.x * kP1Tile, kP1Tile * 4u, bar);
+  }
+  __syncthreads();
 
   for (uint64_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+    if (tid == 0) bulk_wait_read();  // the previous tile's bulk store has read the stage
     for (uint32_t i = tid; i < ncnt; i += kP1Threads) cnt[i] = 0;
     const uint64_t base = t * kP1Tile;
     const uint32_t len = (uint32_t)((n - base) < kP1Tile ? (n - base) : kP1Tile);
+    if (t < full_tiles) {
+      if (!mbar_wait(bar, parity, kCopyPolls)) red[31] = 1;  // the copy never landed: stop (reported below)
+      parity ^= 1u;
+    } else {
+      for (uint32_t i = tid; i < len; i += kP1Threads) kbuf[i] = keys[base + i];
+    }
+    __syncthreads();
+    if (red[31] != 0) break;  // every thread sees the same flag after the barrier
     const uint32_t first = kP1Keys * tid;
     const bool full = first + kP1Keys <= len;
 
     uint32_t kv[kP1Keys];
-    if (full) {
-      const uint4* src = reinterpret_cast<const uint4*>(keys + base + first);
+    const uint4* mine = reinterpret_cast<const uint4*>(kbuf + first);
 #pragma unroll
-      for (uint32_t i = 0; i < kP1Keys / 4; ++i) {
-        const uint4 v = __ldg(src + i);
-        kv[4 * i] = v.x;
-        kv[4 * i + 1] = v.y;
-        kv[4 * i + 2] = v.z;
-        kv[4 * i + 3] = v.w;
-      }
-    } else {
-#pragma unroll
-      for (uint32_t i = 0; i < kP1Keys; ++i) kv[i] = first + i < len ? keys[base + first + i] : 0u;
+    for (uint32_t i = 0; i < kP1Keys / 4; ++i) {
+      const uint4 v = mine[i];
+      kv[4 * i] = v.x;
+      kv[4 * i + 1] = v.y;
+      kv[4 * i + 2] = v.z;
+      kv[4 * i + 3] = v.w;
     }
     // bit i of vm: key i is real and < U (all 16 in the common case, found with one max)
     uint32_t mx = 0;
@@ -117,7 +142,6 @@ __global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t
     for (uint32_t i = 1; i < kP1Keys; ++i) same |= ((kv[i] >> L) == (kv[i - 1] >> L)) ? (1u << i) : 0u;
     same &= vm & (vm << 1);
     const bool runs = __popc(__ballot_sync(0xffffffffu, same != 0)) >= 16;
-    __syncthreads();  // counters zeroed; the previous tile's stage is copied out
 
     // ranks, two 16-bit ranks per register (a (bucket, warp) counter stays below 512)
     uint32_t rk[kP1Keys / 2];
@@ -194,7 +218,15 @@ __global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t
         tcnt[(uint64_t)b * num_tiles + t] = (uint16_t)c;  // bucket-major copy for the split
       }
     }
-    // every key to its slot: base of its (bucket, warp) + its rank
+    // every key to its slot: base of its (bucket, warp) + its rank (keys read again from shared memory)
+#pragma unroll
+    for (uint32_t i = 0; i < kP1Keys / 4; ++i) {
+      const uint4 v = mine[i];
+      kv[4 * i] = v.x;
+      kv[4 * i + 1] = v.y;
+      kv[4 * i + 2] = v.z;
+      kv[4 * i + 3] = v.w;
+    }
     if (vm == 0xffffu) {
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
@@ -210,12 +242,22 @@ __global__ void __launch_bounds__(kP1Threads, 2) partition_kernel(const uint32_t
         }
       }
     }
-    __syncthreads();
-    // write the grouped low parts: tile t owns low[t * 8192 ...]
-    const uint32_t vecs = (tile_valid + 7) / 8;
-    uint4* dst = reinterpret_cast<uint4*>(low + t * kP1Tile);
-    const uint4* st4 = reinterpret_cast<const uint4*>(stage);
-    for (uint32_t v = tid; v < vecs; v += kP1Threads) dst[v] = st4[v];
+    fence_proxy_async_smem();  // the stage writes, before the bulk store reads them
+    __syncthreads();           // every key has been read: the next tile may land in kbuf
+    if (tid == 0) {
+      const uint64_t next = t + gridDim.x;
+      if (next < full_tiles) bulk_load(kbuf, keys + next * kP1Tile, kP1Tile * 4u, bar);
+      // the grouped low parts of tile t: low[t * 8192 ...], rounded up to whole 16-byte pieces
+      const uint32_t bytes = ((tile_valid + 7u) / 8u) * 16u;
+      if (bytes) bulk_store(low + t * kP1Tile, stage, bytes);
+    }
+  }
+  if (tid == 0) {
+    bulk_wait_all();
+    if (red[31] != 0) {
+      raise_error(err, ERRBIT_TIMEOUT);
+      mbar_wait(bar, parity ^ 1u, kCopyPolls);  // give the late copy a last chance to land before exit
+    }
   }
   if (bad) raise_error(err, ERRBIT_KEY_RANGE);
   __syncthreads();
@@ -279,38 +321,38 @@ __global__ void __launch_bounds__(1024) split_kernel(const uint16_t* __restrict_
   const uint32_t base = pbase[b], end = pbase[b + 1];
   if (end <= base || end > max_items) return;  // no parts (or a plan that does not fit: write nothing)
   const uint32_t parts = end - base;
-  uint64_t running = 0;
-  for (uint64_t c = 0; c < num_tiles; c += 1024) {
-    const uint64_t t = c + tid;
-    const uint32_t cnt = t < num_tiles ? (uint32_t)tcnt[(uint64_t)b * num_tiles + t] : 0u;
-    uint32_t x = cnt;
+  // thread tid: tiles [t0, t1) of the bucket's count row, read in one pass
+  const uint64_t per = (num_tiles + 1023) / 1024;
+  const uint64_t t0 = min((uint64_t)tid * per, num_tiles), t1 = min(t0 + per, num_tiles);
+  const uint16_t* row = tcnt + (uint64_t)b * num_tiles;
+  uint32_t local = 0;
+  for (uint64_t t = t0; t < t1; ++t) local += row[t];
+  uint32_t x = local;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= (uint32_t)d) x += y;
+  }
+  if (lane == 31) red[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w0 = red[lane];
+    uint32_t sum = w0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane >= (uint32_t)d) x += y;
+      const uint32_t y = __shfl_up_sync(0xffffffffu, sum, d);
+      if (lane >= (uint32_t)d) sum += y;
     }
-    if (lane == 31) red[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      const uint32_t w0 = red[lane];
-      uint32_t s = w0;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
-        if (lane >= (uint32_t)d) s += y;
-      }
-      red[lane] = s - w0;
-      if (lane == 31) red[32] = s;
-    }
-    __syncthreads();
-    const uint64_t lo = running + red[warp] + (x - cnt), hi = lo + cnt;
-    if (hi > lo) {
-      // parts whose first key falls in this tile start here
-      for (uint64_t p = (lo + item_keys - 1) / item_keys; p * item_keys < hi && p < parts; ++p)
-        items[base + p] = Item{b, (uint32_t)t, 0u, 0u};
-    }
-    running += red[32];
-    __syncthreads();
+    red[lane] = sum - w0;
+  }
+  __syncthreads();
+  // parts whose first key falls in tile t start at t
+  uint64_t lo = red[warp] + (x - local);
+  for (uint64_t t = t0; t < t1; ++t) {
+    const uint64_t hi = lo + row[t];
+    for (uint64_t p = (lo + item_keys - 1) / item_keys; p * item_keys < hi && p < parts; ++p)
+      items[base + p] = Item{b, (uint32_t)t, 0u, 0u};
+    lo = hi;
   }
   __syncthreads();
   for (uint32_t p = tid; p < parts; p += 1024)
@@ -529,7 +571,7 @@ cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint3
 
   cudaError_t e = cudaMemsetAsync(btot, 0, 4 * (size_t)T.B, stream);
   if (e != cudaSuccess) return e;
-  const size_t p1_smem = 4 * (size_t)p1_stage_words(T.B) + 2 * kP1Tile;
+  const size_t p1_smem = 4 * (size_t)p1_words(T.B);
   e = cudaFuncSetAttribute(partition_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

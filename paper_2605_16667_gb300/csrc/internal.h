@@ -20,7 +20,7 @@ struct DeviceInfo {
 // memory of this device as is, page-locked host memory through its mapped
 // address, pageable host memory only where dev.pageable.  INVALID_ARG for
 // memory this device cannot reach.
-dialsort_status_t kernel_address(const void* p, const DeviceInfo& dev, const void** q);
+dialsort_status_t kernel_address(const void* p, const DeviceInfo& dev, const void** q, bool* in_host = nullptr);
 
 // Per-device properties and error word; initialised once per device, with
 // that device current.  Returns nullptr when no device is usable.
