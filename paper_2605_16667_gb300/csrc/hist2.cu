@@ -54,7 +54,9 @@ __host__ __device__ __forceinline__ uint32_t p1_words(uint32_t B) {
 constexpr uint32_t kCopyPolls = 1u << 16;
 
 // ------------------------------------------------------------------ pass 1
-// Thread tid owns keys [16 tid, 16 tid + 16) of the tile.  Each key takes its
+// Warp w owns keys [512 w, 512 w + 512) of the tile; lane l takes the four
+// 16-byte pieces l, l + 32, l + 64, l + 96 of them (4 consecutive keys each),
+// so every shared-memory read of the keys is conflict-free.  Each key takes its
 // rank with one shared-memory atomic on its (bucket, warp) counter and keeps
 // it in a register; a scan turns the counters into bases, and base + rank is
 // the key's slot in the tile's bucket-grouped order.  Runs of one bucket
@@ -108,14 +110,15 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     }
     __syncthreads();
     if (red[31] != 0) break;  // every thread sees the same flag after the barrier
-    const uint32_t first = kP1Keys * tid;
-    const bool full = first + kP1Keys <= len;
+    // key i of this lane: tile position first + 128 (i / 4) + (i % 4)
+    const uint32_t first = kP1Keys * 32u * warp + 4u * lane;
+    const bool full = first + 384u + 4u <= len;  // the lane's last piece is whole
 
     uint32_t kv[kP1Keys];
     const uint4* mine = reinterpret_cast<const uint4*>(kbuf + first);
 #pragma unroll
     for (uint32_t i = 0; i < kP1Keys / 4; ++i) {
-      const uint4 v = mine[i];
+      const uint4 v = mine[32u * i];
       kv[4 * i] = v.x;
       kv[4 * i + 1] = v.y;
       kv[4 * i + 2] = v.z;
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
       vm = 0;
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
-        const bool real = first + i < len;
+        const bool real = first + 128u * (i / 4) + (i % 4) < len;
         const bool ok = kv[i] < U;
         bad |= real && !ok;
         vm |= (real && ok) ? (1u << i) : 0u;
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     // every key to its slot: base of its (bucket, warp) + its rank (keys read again from shared memory)
 #pragma unroll
     for (uint32_t i = 0; i < kP1Keys / 4; ++i) {
-      const uint4 v = mine[i];
+      const uint4 v = mine[32u * i];
       kv[4 * i] = v.x;
       kv[4 * i + 1] = v.y;
       kv[4 * i + 2] = v.z;
