@@ -78,13 +78,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch for `kernel` from the committed ncu summary, if it was taken on this source."""
+def ncu_traffic(phase: str):
+    """DRAM bytes of one launch of `phase` ("histogram" or "reconstruct") at the benchmark size, from the
+    committed ncu summary (profiles/traffic.json), only if it was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d[kernel]
+        e = d[phase]
         if e.get("source_hash") != kernel_source_hash():
             return None
         return e["bytes_per_launch_full"]
@@ -485,9 +486,9 @@ def main():
     hist_bytes = w * n + 8 * U   # read keys, zero H, write H
     recon_bytes = w * n + 4 * U  # read H, write the keys
     if hist_ms >= recon_ms:
-        dom, dom_bytes, dom_ms, kname = "histogram (zero H + ingest)", hist_bytes, hist_ms, "hist_kernel"
+        dom, dom_bytes, dom_ms, kname = "histogram (zero H + ingest)", hist_bytes, hist_ms, "histogram"
     else:
-        dom, dom_bytes, dom_ms, kname = "reconstruct (offsets + expand)", recon_bytes, recon_ms, "expand_kernel"
+        dom, dom_bytes, dom_ms, kname = "reconstruct (offsets + expand)", recon_bytes, recon_ms, "reconstruct"
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": ncu_traffic(kname), "kernel": dom, "peak_source": peak_kind,
@@ -531,13 +532,15 @@ def main():
     staged_value = time_e2e(staged_step, e2e_steps)
     head = pin_out.numpy()[: 1 << 20].view(np.uint32 if w == 4 else np.uint16)
     e2e_ok = bool(np.all(head[1:] >= head[:-1])) if e2e_steps else None
-    e2e = {"value": staged_value, "unit": "keys/s",
+    staged = {"value": staged_value, "how": "pinned host keys copied in (cudaMemcpyAsync), dialsort_sort on the "
+              "device, sorted keys copied out; copies inside the timed region"}
+    zero_copy = {"value": e2e_value, "how": "dialsort_sort given the pinned host buffers themselves: its kernels "
+                 "read and write host memory across the CPU-GPU link"}
+    best, other = (staged, zero_copy) if (staged_value or 0) >= (e2e_value or 0) else (zero_copy, staged)
+    e2e = {"value": best["value"], "unit": "keys/s",
            "h2d_bytes_per_step": w * n, "d2h_bytes_per_step": w * n, "steps": e2e_steps,
-           "host_output_sorted": e2e_ok,
-           "how": "pinned host keys copied in (cudaMemcpyAsync), dialsort_sort on the device, sorted keys "
-                  "copied out; copies inside the timed region",
-           "zero_copy": {"value": e2e_value, "how": "dialsort_sort given the pinned host buffers themselves: "
-                         "its kernels read and write host memory across the CPU-GPU link"}}
+           "host_output_sorted": e2e_ok, "how": best["how"] + " (the faster of two host-buffer forms)",
+           "other_form": other}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

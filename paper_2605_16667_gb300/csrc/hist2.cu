@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(1024) split_kernel(const uint16_t* __restrict_
 constexpr uint32_t kP2Threads = 512;
 constexpr uint32_t kP2Warps = kP2Threads / 32;
 constexpr uint32_t kP2Unroll = 4;
-constexpr uint32_t kP2LongSegment = 16;  // mean chunks per tile from which a warp takes one tile at a time
+constexpr uint32_t kP2LongSegment = 48;  // mean chunks per tile from which a warp takes one tile at a time
 
 // Count one chunk per lane (all 32 lanes call this together).  A chunk of
 // eight equal low parts (a hot or repeated key) is one item (key, 8) -- the
@@ -522,7 +522,10 @@ TwoLevelLayout two_level_layout(uint64_t n, uint32_t U) {
   TwoLevelLayout T;
   uint32_t lg = 0;
   while (lg < 32 && (1ull << lg) < U) ++lg;
-  T.L = std::min<uint32_t>(16, std::max<uint32_t>(8, lg > 7 ? lg - 7 : 8));
+  // Low bits per key: 64 buckets up to U = 2^20 and 128 beyond, while the pass-2 histogram (2^L
+  // 32-bit counters) still fits 64 KB for two CTAs per SM; past that, packed 16-bit counters.
+  T.L = lg <= 20 ? std::min<uint32_t>(14, std::max<uint32_t>(8, lg > 6 ? lg - 6 : 8))
+                 : std::min<uint32_t>(16, lg - 7);
   T.B = (uint32_t)(((uint64_t)U + (1ull << T.L) - 1) >> T.L);
   T.num_tiles = (n + kP1Tile - 1) / kP1Tile;
   const uint64_t bins = 1ull << T.L;
