@@ -365,14 +365,12 @@ __global__ void __launch_bounds__(1024) split_kernel(const uint16_t* __restrict_
 // ------------------------------------------------------------------ pass 2
 // Two ways to spread an item's chunks (16-byte pieces of its segments) over
 // the warps, chosen per item from the mean segment length:
-//   short segments (uniform keys: ~9 chunks per tile): warp w takes the
-//     item's tiles 32 at a time (lane l: one tile); the chunks of those 32
-//     segments are numbered flat (a warp scan) and lane l takes chunks l,
-//     l + 32, ..., finding each chunk's tile by a 5-step binary search over
-//     the scan held in the lanes;
+//   short segments (uniform keys: ~17 chunks per tile): warp w takes the
+//     item's tiles 32 at a time and lane l walks the segment of tile l chunk
+//     by chunk, the warp stepping as long as its longest segment;
 //   long segments (a hot bucket, sorted or repeated keys): warp w takes
 //     tiles w, w + 16, ... and its lanes stride through each segment.
-// Either way every lane has chunks to load.  Low parts need no range check:
+// Either way the lanes stay busy.  Low parts need no range check:
 // pass 1 dropped every key >= U.
 constexpr uint32_t kP2Threads = 512;
 constexpr uint32_t kP2Warps = kP2Threads / 32;
@@ -466,7 +464,8 @@ __global__ void __launch_bounds__(kP2Threads, 2) bucket_kernel(const uint16_t* _
     }
   } else {
     for (uint64_t tb = it.t0 + (uint64_t)warp * 32u; tb < it.t1; tb += kP2Warps * 32u) {
-      // this lane's tile: the bucket's segment [a0, a1) and its chunks [a0 / 8, ceil(a1 / 8))
+      // lane l walks the bucket's segment [a0, a1) of tile tb + l, 16-byte chunk by chunk; the warp runs as
+      // many steps as its longest segment
       const uint64_t t = tb + lane;
       uint32_t a0 = 0, a1 = 0;
       if (t < it.t1) {
@@ -474,37 +473,23 @@ __global__ void __launch_bounds__(kP2Threads, 2) bucket_kernel(const uint16_t* _
         a0 = row[it.bucket];
         a1 = row[it.bucket + 1];
       }
-      const uint32_t nb = a1 > a0 ? ((a1 + 7u) >> 3) - (a0 >> 3) : 0u;
-      uint32_t incl = nb;
+      const uint32_t c_lo = a0 >> 3;
+      const uint32_t nch = a1 > a0 ? ((a1 + 7u) >> 3) - c_lo : 0u;
+      uint32_t steps = nch;
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= (uint32_t)d) incl += y;
-      }
-      const uint32_t excl = incl - nb;
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      for (uint32_t j0 = 0; j0 < total; j0 += 32u * kP2Unroll) {
+      for (int d = 16; d > 0; d >>= 1) steps = max(steps, __shfl_xor_sync(0xffffffffu, steps, d));
+      const uint4* tile4 = low4 + (t < it.t1 ? t : it.t0) * (uint64_t)(kP1Tile / 8);
+      for (uint32_t i = 0; i < steps; i += kP2Unroll) {  // warp-uniform bound: count_chunk is a warp collective
         uint4 q[kP2Unroll];
         uint32_t vm[kP2Unroll];
 #pragma unroll
         for (uint32_t u = 0; u < kP2Unroll; ++u) {
-          const uint32_t j = j0 + u * 32u + lane;
-          // the chunk's tile: the last lane l with excl_l <= j (lanes with no chunks are never it)
-          uint32_t l = 0;
-#pragma unroll
-          for (uint32_t step = 16; step != 0; step >>= 1) {
-            const uint32_t e = __shfl_sync(0xffffffffu, excl, l + step);
-            if (e <= j) l += step;
-          }
-          const uint32_t sa = __shfl_sync(0xffffffffu, a0, l);
-          const uint32_t sb = __shfl_sync(0xffffffffu, a1, l);
-          const uint32_t el = __shfl_sync(0xffffffffu, excl, l);
           vm[u] = 0;
           q[u] = make_uint4(0u, 0u, 0u, 0u);
-          if (j < total) {
-            const uint32_t c = (sa >> 3) + (j - el);  // chunk within the tile
-            vm[u] = chunk_mask(sa, sb, c * 8u);
-            q[u] = __ldg(low4 + (tb + l) * (uint64_t)(kP1Tile / 8) + c);
+          if (i + u < nch) {
+            const uint32_t c = c_lo + i + u;
+            vm[u] = chunk_mask(a0, a1, c * 8u);
+            q[u] = __ldg(tile4 + c);
           }
         }
 #pragma unroll

@@ -219,25 +219,29 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
   const uint64_t tile_hi = min(tile_lo + kTileKeys, total);
   const uint32_t len = (uint32_t)(tile_hi - tile_lo);
 
-  uint4* M4 = reinterpret_cast<uint4*>(M);
-  for (uint32_t i = tid; i < kTileKeys / 4; i += kReconThreads) M4[i] = make_uint4(0u, 0u, 0u, 0u);
-  if (tid == 0) {
-    sm.nruns = 0;
-    sm.nlong = 0;
-  }
-  __syncthreads();
-
   // Mark run starts of every chunk overlapping [tile_lo, tile_hi).  A dense
   // tile overlaps one or two chunks: the whole CTA scans each (4 bins per
   // thread, one load each).  A sparse tile can overlap hundreds: the chunks
   // are shared out among the warps (warp w: c0 + w, c0 + w + 8, ...), each
   // warp scans its chunk with shuffles alone and skips an empty chunk without
-  // reading its bins.
+  // reading its bins.  Every run crossing the tile is also noted (up to
+  // kPaintRuns) so that a tile of few runs can be painted; a dense tile first
+  // only notes runs and writes the marks in a second scan if it has too many.
   const uint64_t c0 = first_chunk[tile];
   const uint64_t num_tiles = (n_cap + kTileKeys - 1) / kTileKeys;
   // the next tile's first chunk bounds the chunks this tile can overlap
   const uint64_t c_last = (tile + 1 < num_tiles && tile_hi < total) ? first_chunk[tile + 1] : num_chunks - 1;
-  if (c_last - c0 <= 1) {
+  const bool dense = c_last - c0 <= 1;
+  uint4* M4 = reinterpret_cast<uint4*>(M);
+  if (!dense)
+    for (uint32_t i = tid; i < kTileKeys / 4; i += kReconThreads) M4[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) {
+    sm.nruns = 0;
+    sm.nlong = 0;
+  }
+  __syncthreads();
+  // dense tiles: notes (marks == false) or marks (marks == true) from one CTA-wide scan per chunk
+  auto dense_scan = [&](bool marks) {
     for (uint64_t c = c0; c <= c_last && c < num_chunks; ++c) {
       const uint64_t oc = O[c];
       if (oc >= tile_hi) break;
@@ -254,16 +258,23 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
           const uint32_t mark = (uint32_t)(b0 + j) + 1u;
           const uint32_t e = (uint32_t)((end < tile_hi ? end : tile_hi) - tile_lo);
           if (start >= tile_lo && start < tile_hi) {
-            M[start - tile_lo] = mark;
-            note_run(sm, (uint32_t)(start - tile_lo), e, mark - 1u);
+            if (marks)
+              M[start - tile_lo] = mark;
+            else
+              note_run(sm, (uint32_t)(start - tile_lo), e, mark - 1u);
           } else if (start < tile_lo && end > tile_lo) {
-            M[0] = mark;
-            note_run(sm, 0u, e, mark - 1u);
+            if (marks)
+              M[0] = mark;
+            else
+              note_run(sm, 0u, e, mark - 1u);
           }
         }
         sc += h[j];
       }
     }
+  };
+  if (dense) {
+    dense_scan(false);
   } else {
     for (uint64_t c = c0 + warp; c < num_chunks; c += kReconThreads / 32) {
       const uint64_t oc = O[c];
@@ -321,6 +332,12 @@ __device__ __forceinline__ void expand_tile(const uint32_t* __restrict__ H, uint
     }
     __syncthreads();  // sm is reused by the caller's next item
     return;
+  }
+  if (dense) {  // too many runs to paint: the marks, from a second scan
+    for (uint32_t i = tid; i < kTileKeys / 4; i += kReconThreads) M4[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    dense_scan(true);
+    __syncthreads();
   }
 
   // Fill forward: every slot takes the latest mark at or before it.  Warp w
