@@ -145,12 +145,22 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     for (uint32_t i = 1; i < kP1Keys; ++i) same |= ((kv[i] >> L) == (kv[i - 1] >> L)) ? (1u << i) : 0u;
     same &= vm & (vm << 1);
     const bool runs = __popc(__ballot_sync(0xffffffffu, same != 0)) >= 16;
+    // the whole warp in one bucket (sorted or repeated keys): one atomic for its 512 keys, and ranks laid
+    // out so that every stage store below writes 32 consecutive slots
+    const uint32_t b0 = __shfl_sync(0xffffffffu, kv[0] >> L, 0);  // in every lane: no short circuit
+    const bool one_bucket = __all_sync(0xffffffffu, vm == 0xffffu && same == 0xfffeu && (kv[0] >> L) == b0);
 
     // ranks, two 16-bit ranks per register (a (bucket, warp) counter stays below 512)
     uint32_t rk[kP1Keys / 2];
 #pragma unroll
     for (uint32_t i = 0; i < kP1Keys / 2; ++i) rk[i] = 0;
-    if (runs) {
+    if (one_bucket) {
+      uint32_t r0 = 0;
+      if (lane == 0) r0 = atomicAdd(cnt + b0 * kCntStride + warp, kP1Keys * 32u);
+      r0 = __shfl_sync(0xffffffffu, r0, 0) + lane;
+#pragma unroll
+      for (uint32_t i = 0; i < kP1Keys; ++i) rk[i / 2] |= (r0 + 32u * i) << (16 * (i & 1));
+    } else if (runs) {
       uint32_t r = 0;
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
@@ -367,7 +377,10 @@ __global__ void __launch_bounds__(1024) split_kernel(const uint16_t* __restrict_
 // the warps, chosen per item from the mean segment length:
 //   short segments (uniform keys: ~17 chunks per tile): warp w takes the
 //     item's tiles 32 at a time and lane l walks the segment of tile l chunk
-//     by chunk, the warp stepping as long as its longest segment;
+//     by chunk, the warp stepping as long as its longest segment; when that
+//     would leave most lanes idle (a few long segments among empty ones),
+//     the 32 segments' chunks are numbered flat instead and lane l takes
+//     chunks l, l + 32, ..., found by a binary search over the warp's scan;
 //   long segments (a hot bucket, sorted or repeated keys): warp w takes
 //     tiles w, w + 16, ... and its lanes stride through each segment.
 // Either way the lanes stay busy.  Low parts need no range check:
@@ -464,8 +477,7 @@ __global__ void __launch_bounds__(kP2Threads, 2) bucket_kernel(const uint16_t* _
     }
   } else {
     for (uint64_t tb = it.t0 + (uint64_t)warp * 32u; tb < it.t1; tb += kP2Warps * 32u) {
-      // lane l walks the bucket's segment [a0, a1) of tile tb + l, 16-byte chunk by chunk; the warp runs as
-      // many steps as its longest segment
+      // lane l: the bucket's segment [a0, a1) of tile tb + l and its chunks [a0 / 8, ceil(a1 / 8))
       const uint64_t t = tb + lane;
       uint32_t a0 = 0, a1 = 0;
       if (t < it.t1) {
@@ -475,25 +487,90 @@ __global__ void __launch_bounds__(kP2Threads, 2) bucket_kernel(const uint16_t* _
       }
       const uint32_t c_lo = a0 >> 3;
       const uint32_t nch = a1 > a0 ? ((a1 + 7u) >> 3) - c_lo : 0u;
-      uint32_t steps = nch;
+      uint32_t steps = nch, incl = nch;
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) steps = max(steps, __shfl_xor_sync(0xffffffffu, steps, d));
-      const uint4* tile4 = low4 + (t < it.t1 ? t : it.t0) * (uint64_t)(kP1Tile / 8);
-      for (uint32_t i = 0; i < steps; i += kP2Unroll) {  // warp-uniform bound: count_chunk is a warp collective
-        uint4 q[kP2Unroll];
-        uint32_t vm[kP2Unroll];
 #pragma unroll
-        for (uint32_t u = 0; u < kP2Unroll; ++u) {
-          vm[u] = 0;
-          q[u] = make_uint4(0u, 0u, 0u, 0u);
-          if (i + u < nch) {
-            const uint32_t c = c_lo + i + u;
-            vm[u] = chunk_mask(a0, a1, c * 8u);
-            q[u] = __ldg(tile4 + c);
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= (uint32_t)d) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total >= 32u * kP2LongSegment) {
+        // long segments in this batch (a hot bucket, sorted runs): the warp takes the 32 tiles one at a
+        // time and its lanes stride through each segment, so equal chunks meet in one warp step
+        for (uint32_t k = 0; k < 32u; ++k) {
+          const uint32_t ka0 = __shfl_sync(0xffffffffu, a0, k), ka1 = __shfl_sync(0xffffffffu, a1, k);
+          if (ka1 <= ka0) continue;  // warp-uniform
+          const uint32_t c_end = (ka1 + 7u) >> 3;
+          const uint4* tile4 = low4 + (tb + k) * (uint64_t)(kP1Tile / 8);
+          for (uint32_t c0 = ka0 >> 3; c0 < c_end; c0 += 32u * kP2Unroll) {
+            uint4 q[kP2Unroll];
+            uint32_t vm[kP2Unroll];
+#pragma unroll
+            for (uint32_t u = 0; u < kP2Unroll; ++u) {
+              const uint32_t c = c0 + 32u * u + lane;
+              vm[u] = 0;
+              q[u] = make_uint4(0u, 0u, 0u, 0u);
+              if (c < c_end) {
+                vm[u] = chunk_mask(ka0, ka1, c * 8u);
+                q[u] = __ldg(tile4 + c);
+              }
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u], lane);
           }
         }
+      } else if (2u * total >= 32u * steps) {
+        // balanced: each lane walks its own segment (at least half the lanes busy at every step)
+        const uint4* tile4 = low4 + (t < it.t1 ? t : it.t0) * (uint64_t)(kP1Tile / 8);
+        for (uint32_t i = 0; i < steps; i += kP2Unroll) {  // warp-uniform bound: count_chunk is a warp collective
+          uint4 q[kP2Unroll];
+          uint32_t vm[kP2Unroll];
 #pragma unroll
-        for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u], lane);
+          for (uint32_t u = 0; u < kP2Unroll; ++u) {
+            vm[u] = 0;
+            q[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (i + u < nch) {
+              const uint32_t c = c_lo + i + u;
+              vm[u] = chunk_mask(a0, a1, c * 8u);
+              q[u] = __ldg(tile4 + c);
+            }
+          }
+#pragma unroll
+          for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u], lane);
+        }
+      } else {
+        // unbalanced (a few long segments among empty ones): number the 32 segments' chunks flat and let
+        // lane l take chunks l, l + 32, ..., finding each chunk's tile by a 5-step binary search over the
+        // scan held in the lanes
+        const uint32_t excl = incl - nch;
+        for (uint32_t j0 = 0; j0 < total; j0 += 32u * kP2Unroll) {
+          uint4 q[kP2Unroll];
+          uint32_t vm[kP2Unroll];
+#pragma unroll
+          for (uint32_t u = 0; u < kP2Unroll; ++u) {
+            const uint32_t j = j0 + u * 32u + lane;
+            uint32_t l = 0;  // the last lane with excl_l <= j (lanes without chunks are never it)
+#pragma unroll
+            for (uint32_t step = 16; step != 0; step >>= 1) {
+              const uint32_t e = __shfl_sync(0xffffffffu, excl, l + step);
+              if (e <= j) l += step;
+            }
+            const uint32_t sa = __shfl_sync(0xffffffffu, a0, l);
+            const uint32_t sb = __shfl_sync(0xffffffffu, a1, l);
+            const uint32_t el = __shfl_sync(0xffffffffu, excl, l);
+            vm[u] = 0;
+            q[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (j < total) {
+              const uint32_t c = (sa >> 3) + (j - el);  // chunk within tile tb + l
+              vm[u] = chunk_mask(sa, sb, c * 8u);
+              q[u] = __ldg(low4 + (tb + l) * (uint64_t)(kP1Tile / 8) + c);
+            }
+          }
+#pragma unroll
+          for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u], lane);
+        }
       }
     }
   }
