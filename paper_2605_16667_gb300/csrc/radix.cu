@@ -111,7 +111,6 @@ struct RxSmem {
   uint32_t in[kRxTile];                  // the tile's keys in input order (frees registers across the scan)
   uint32_t stage[kRxTile];               // the tile's keys in stable digit order
   uint16_t wcnt[kRxWarps][kRxDigits];    // per-warp digit counters, then per-warp digit bases
-  uint32_t tstart[kRxDigits + 1];        // digit starts within the tile
   uint32_t gpos[kRxDigits];              // global position of the tile's first key of each digit
   uint32_t gbase[kRxDigits];             // global start of each digit
   uint32_t next[kRxDigits];              // histogram of the next pass's digit (this CTA)
@@ -212,19 +211,6 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_pass_kernel(const uint32_t* 
       else
         rk[i / 2] |= r << 16;
     }
-    if (count_next) {  // the next pass's digit, from the keys kept in shared memory
-#pragma unroll 4
-      for (uint32_t i = 0; i < kRxSteps; ++i) {
-        const bool valid = base + 32u * i + lane < n;
-        const uint32_t dn = rx_digit(in[32u * i], pass + 1, kSigned);
-        const uint32_t d0 = __shfl_sync(0xffffffffu, dn, 0);  // every lane takes part (no short circuit)
-        if (__all_sync(0xffffffffu, valid && dn == d0)) {
-          if (lane == 0) atomicAdd(&S.next[dn], 32u);
-        } else if (valid) {
-          atomicAdd(&S.next[dn], 1u);
-        }
-      }
-    }
     __syncthreads();
 
     // per digit: warp bases (in place) and the tile's count; then digit starts in the tile
@@ -240,14 +226,14 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_pass_kernel(const uint32_t* 
     uint32_t tile_valid;
     const uint32_t start = scan256(cnt, S.red, &tile_valid);
     if (tid < kRxDigits) {
-      S.tstart[tid] = start;
-      if (tid == 0) S.tstart[kRxDigits] = tile_valid;
+#pragma unroll
+      for (uint32_t w = 0; w < kRxWarps; ++w) S.wcnt[w][tid] = (uint16_t)(S.wcnt[w][tid] + start);
       // publish this tile's count, then look back over earlier tiles for the digit's prefix
       uint64_t* my = desc + t * kRxDigits + tid;
       const uint32_t agg = 2u * pass + 1u, inc = 2u * pass + 2u;
       if (t == 0) {
         st_release_u64(my, rx_desc(inc, cnt));
-        S.gpos[tid] = S.gbase[tid];
+        S.gpos[tid] = S.gbase[tid] - start;
       } else {
         st_release_u64(my, rx_desc(agg, cnt));
         uint32_t prefix = 0;
@@ -273,7 +259,7 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_pass_kernel(const uint32_t* 
           __nanosleep(64);
         }
         st_release_u64(my, rx_desc(inc, prefix + cnt));
-        S.gpos[tid] = S.gbase[tid] + prefix;
+        S.gpos[tid] = S.gbase[tid] + prefix - start;
       }
     }
     __syncthreads();
@@ -285,16 +271,30 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_pass_kernel(const uint32_t* 
         const uint32_t x = in[32u * i];
         const uint32_t d = rx_digit(x, pass, kSigned);
         const uint32_t r = (rk[i / 2] >> (16 * (i & 1))) & 0xffffu;
-        S.stage[S.tstart[d] + S.wcnt[warp][d] + r] = x;
+        S.stage[S.wcnt[warp][d] + r] = x;
       }
     }
     __syncthreads();
     // write out: consecutive slots of one digit go to consecutive addresses
-    for (uint32_t j = tid; j < tile_valid; j += kRxThreads) {
-      const uint32_t x = S.stage[j];
-      const uint32_t d = rx_digit(x, pass, kSigned);
-      const uint64_t pos = (uint64_t)S.gpos[d] + (j - S.tstart[d]);
-      if (pos < n) dst[pos] = x;  // always true unless a look-back timed out
+    // write out: consecutive slots of one digit go to consecutive addresses; the next pass's digit is
+    // counted on the way (gpos[d] holds the digit's global start minus its start in the tile)
+    for (uint32_t j0 = warp * 32u; j0 < tile_valid; j0 += kRxThreads) {  // warp-uniform bound
+      const uint32_t j = j0 + lane;
+      const bool valid = j < tile_valid;
+      const uint32_t x = valid ? S.stage[j] : 0u;
+      if (valid) {
+        const uint32_t pos = S.gpos[rx_digit(x, pass, kSigned)] + j;  // mod 2^32: exact, since n < 2^32
+        if (pos < n) dst[pos] = x;  // always true unless a look-back timed out
+      }
+      if (count_next) {  // one add of 32 when the warp's keys share the next digit (small keys, a constant byte)
+        const uint32_t dn = rx_digit(x, pass + 1, kSigned);
+        const uint32_t d0 = __shfl_sync(0xffffffffu, dn, 0);
+        if (__all_sync(0xffffffffu, valid && dn == d0)) {
+          if (lane == 0) atomicAdd(&S.next[dn], 32u);
+        } else if (valid) {
+          atomicAdd(&S.next[dn], 1u);
+        }
+      }
     }
     __syncthreads();
   }
