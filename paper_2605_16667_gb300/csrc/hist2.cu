@@ -38,13 +38,10 @@ struct Item {
 };
 
 
-// Pass-1 counters: one per (bucket, half-warp), bucket-major with a stride of
-// kP1Groups + 1 words, so one bucket's counters are contiguous for the scan
-// while a half-warp's buckets spread over all banks.  Half-warps rather than
-// warps: an atomic instruction then spreads 16 lanes, not 32, over the banks
-// of its counters, which roughly halves its bank conflicts.
-constexpr uint32_t kP1Groups = 2 * kP1Warps;
-constexpr uint32_t kCntStride = kP1Groups + 1;
+// Pass-1 counters: one per (bucket, warp), bucket-major with a stride of
+// kP1Warps + 1 words, so one bucket's warp counters are contiguous for the
+// scan while one warp's buckets spread over all banks for the atomics.
+constexpr uint32_t kCntStride = kP1Warps + 1;
 
 // Pass-1 shared memory, in 32-bit words: the tile's keys (filled by a bulk
 // copy), the staged low parts, the counters, the bucket totals, scan scratch
@@ -60,7 +57,7 @@ constexpr uint32_t kCopyPolls = 1u << 16;
 // Warp w owns keys [512 w, 512 w + 512) of the tile; lane l takes the four
 // 16-byte pieces l, l + 32, l + 64, l + 96 of them (4 consecutive keys each),
 // so every shared-memory read of the keys is conflict-free.  Each key takes its
-// rank with one shared-memory atomic on its (bucket, half-warp) counter and keeps
+// rank with one shared-memory atomic on its (bucket, warp) counter and keeps
 // it in a register; a scan turns the counters into bases, and base + rank is
 // the key's slot in the tile's bucket-grouped order.  Runs of one bucket
 // within a thread (skew, sorted input, repeated keys) take one atomic per
@@ -85,7 +82,6 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
   uint32_t* red = bacc + B;                                      // [32] scan scratch; red[31]: stop flag
   uint64_t* bar = reinterpret_cast<uint64_t*>(red + 32);         // the key copy's mbarrier
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  const uint32_t grp = tid >> 4;  // this thread's half-warp: its counter column
   const uint32_t lowmask = (1u << L) - 1u;
   const uint32_t ncnt = B * kCntStride;
   const uint64_t full_tiles = n / kP1Tile;  // tiles loaded by a bulk copy; the ragged last one by plain loads
@@ -149,28 +145,28 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     for (uint32_t i = 1; i < kP1Keys; ++i) same |= ((kv[i] >> L) == (kv[i - 1] >> L)) ? (1u << i) : 0u;
     same &= vm & (vm << 1);
     const bool runs = __popc(__ballot_sync(0xffffffffu, same != 0)) >= 16;
-    // the whole warp in one bucket (sorted or repeated keys): one atomic per half-warp for its 256 keys,
-    // and ranks laid out so that every stage store below writes two runs of 16 consecutive slots
+    // the whole warp in one bucket (sorted or repeated keys): one atomic for its 512 keys, and ranks laid
+    // out so that every stage store below writes 32 consecutive slots
     const uint32_t b0 = __shfl_sync(0xffffffffu, kv[0] >> L, 0);  // in every lane: no short circuit
     const bool one_bucket = __all_sync(0xffffffffu, vm == 0xffffu && same == 0xfffeu && (kv[0] >> L) == b0);
 
-    // ranks, two 16-bit ranks per register (a (bucket, half-warp) counter stays below 256)
+    // ranks, two 16-bit ranks per register (a (bucket, warp) counter stays below 512)
     uint32_t rk[kP1Keys / 2];
 #pragma unroll
     for (uint32_t i = 0; i < kP1Keys / 2; ++i) rk[i] = 0;
     if (one_bucket) {
       uint32_t r0 = 0;
-      if ((lane & 15u) == 0) r0 = atomicAdd(cnt + b0 * kCntStride + grp, kP1Keys * 16u);
-      r0 = __shfl_sync(0xffffffffu, r0, lane & 16u) + (lane & 15u);
+      if (lane == 0) r0 = atomicAdd(cnt + b0 * kCntStride + warp, kP1Keys * 32u);
+      r0 = __shfl_sync(0xffffffffu, r0, 0) + lane;
 #pragma unroll
-      for (uint32_t i = 0; i < kP1Keys; ++i) rk[i / 2] |= (r0 + 16u * i) << (16 * (i & 1));
+      for (uint32_t i = 0; i < kP1Keys; ++i) rk[i / 2] |= (r0 + 32u * i) << (16 * (i & 1));
     } else if (runs) {
       uint32_t r = 0;
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
         if ((vm >> i) & 1u) {
           if (!((same >> i) & 1u))  // a run starts here; its length counts the ones after it
-            r = atomicAdd(cnt + (kv[i] >> L) * kCntStride + grp, (uint32_t)__ffs(~(same >> (i + 1))));
+            r = atomicAdd(cnt + (kv[i] >> L) * kCntStride + warp, (uint32_t)__ffs(~(same >> (i + 1))));
           else
             ++r;
         }
@@ -179,22 +175,22 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     } else if (vm == 0xffffu) {
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i)
-        rk[i / 2] |= atomicAdd(cnt + (kv[i] >> L) * kCntStride + grp, 1u) << (16 * (i & 1));
+        rk[i / 2] |= atomicAdd(cnt + (kv[i] >> L) * kCntStride + warp, 1u) << (16 * (i & 1));
     } else {
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
-        const uint32_t r = ((vm >> i) & 1u) ? atomicAdd(cnt + (kv[i] >> L) * kCntStride + grp, 1u) : 0u;
+        const uint32_t r = ((vm >> i) & 1u) ? atomicAdd(cnt + (kv[i] >> L) * kCntStride + warp, 1u) : 0u;
         rk[i / 2] |= r << (16 * (i & 1));
       }
     }
     __syncthreads();
 
-    // bucket-major, half-warp-minor exclusive scan of the counts -> bases (in place)
-    const uint32_t E = kP1Groups * B;
+    // bucket-major, warp-minor exclusive scan of the counts -> bases (in place)
+    const uint32_t E = kP1Warps * B;
     const uint32_t per = (E + kP1Threads - 1) / kP1Threads;
     const uint32_t e0 = min(tid * per, E), e1 = min(e0 + per, E);
     uint32_t local = 0;
-    for (uint32_t e = e0; e < e1; ++e) local += cnt[(e / kP1Groups) * kCntStride + e % kP1Groups];
+    for (uint32_t e = e0; e < e1; ++e) local += cnt[(e / kP1Warps) * kCntStride + e % kP1Warps];
     uint32_t x = local;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -217,7 +213,7 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     __syncthreads();
     uint32_t acc = red[warp] + (x - local);
     for (uint32_t e = e0; e < e1; ++e) {
-      uint32_t* c = &cnt[(e / kP1Groups) * kCntStride + e % kP1Groups];
+      uint32_t* c = &cnt[(e / kP1Warps) * kCntStride + e % kP1Warps];
       const uint32_t v = *c;
       *c = acc;
       acc += v;
@@ -235,7 +231,7 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
         tcnt[(uint64_t)b * num_tiles + t] = (uint16_t)c;  // bucket-major copy for the split
       }
     }
-    // every key to its slot: base of its (bucket, half-warp) + its rank (keys read again from shared memory)
+    // every key to its slot: base of its (bucket, warp) + its rank (keys read again from shared memory)
 #pragma unroll
     for (uint32_t i = 0; i < kP1Keys / 4; ++i) {
       const uint4 v = mine[32u * i];
@@ -248,14 +244,14 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
         const uint32_t r = (rk[i / 2] >> (16 * (i & 1))) & 0xffffu;
-        stage[cnt[(kv[i] >> L) * kCntStride + grp] + r] = (uint16_t)(kv[i] & lowmask);
+        stage[cnt[(kv[i] >> L) * kCntStride + warp] + r] = (uint16_t)(kv[i] & lowmask);
       }
     } else {
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
         if ((vm >> i) & 1u) {
           const uint32_t r = (rk[i / 2] >> (16 * (i & 1))) & 0xffffu;
-          stage[cnt[(kv[i] >> L) * kCntStride + grp] + r] = (uint16_t)(kv[i] & lowmask);
+          stage[cnt[(kv[i] >> L) * kCntStride + warp] + r] = (uint16_t)(kv[i] & lowmask);
         }
       }
     }
