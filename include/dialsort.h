@@ -68,11 +68,14 @@ typedef enum {
   DIALSORT_REGIME_AUTO = 0,
   DIALSORT_REGIME_SMEM32 = 1,     /* per-CTA 32-bit sub-histograms in shared memory, merged into H */
   DIALSORT_REGIME_SMEM16 = 2,     /* per-CTA packed 16-bit sub-histograms with exact carry spill */
-  DIALSORT_REGIME_CLUSTER = 3,    /* one packed sub-histogram spread over a CTA cluster's shared memory */
+  DIALSORT_REGIME_CLUSTER = 3,    /* reserved: a sub-histogram spread over a cluster's shared memory; not
+                                     built (remote shared-memory atomics measured slower than L2 ones),
+                                     refused with DIALSORT_ERR_INVALID_ARG */
   DIALSORT_REGIME_GLOBAL_CRN = 4, /* warp CRN, then one L2 atomic per distinct key of the warp */
   DIALSORT_REGIME_GLOBAL = 5,     /* one L2 atomic per key run of a thread (no cross-lane merge) */
   DIALSORT_REGIME_TWO_LEVEL = 6,  /* large U: partition keys by high bits, then count low bits in shared
-                                     memory per bucket (needs workspace; uint32 keys, 16-byte aligned) */
+                                     memory per bucket (needs workspace; uint32 keys in device memory,
+                                     16-byte aligned) */
 } dialsort_regime_t;
 
 /* Launch choices for step 1.  Zero in any field means "pick automatically". */
@@ -115,8 +118,10 @@ size_t dialsort_histogram_workspace_size(uint64_t n, uint32_t U, uint32_t key_by
 /*
  * As dialsort_histogram_ex with a workspace (256-byte aligned device memory,
  * not shared with concurrent calls).  With enough workspace the automatic
- * plan uses the two-level regime for large universes (uint32 keys, 16-byte
- * aligned, n >= 2^20); ws may be NULL (then it never does).
+ * plan uses the two-level regime for large universes (uint32 keys in device
+ * memory, 16-byte aligned, n >= 2^20); ws may be NULL (then it never does).
+ * Forcing DIALSORT_REGIME_TWO_LEVEL on keys that do not qualify returns
+ * DIALSORT_ERR_INVALID_ARG (DIALSORT_ERR_WORKSPACE if only ws is short).
  */
 dialsort_status_t dialsort_histogram_ws(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H,
                                         const dialsort_hist_config_t* cfg, void* ws, size_t ws_bytes,
