@@ -396,10 +396,16 @@ constexpr uint32_t kP2LongSegment = 48;  // mean chunks per tile from which a wa
 // are merged across the warp (match.any, the CRN's equality merge) and one
 // lane adds their sum, so sorted or repeated keys do not pile 32 lanes onto
 // one shared-memory address.
-template <int MODE>
+template <int MODE, bool kMerge = true>
 __device__ __forceinline__ void count_chunk(const Sink<MODE>& s, const uint4& q, uint32_t vm, uint32_t lane) {
   const uint32_t k[8] = {q.x & 0xffffu, q.x >> 16, q.y & 0xffffu, q.y >> 16,
                          q.z & 0xffffu, q.z >> 16, q.w & 0xffffu, q.w >> 16};
+  if (!kMerge) {  // short segments: runs of one low part are rare, plain adds
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i)
+      if ((vm >> i) & 1u) s.add(k[i], 1u);
+    return;
+  }
   const bool same8 = vm == 0xffu && q.x == q.y && q.x == q.z && q.x == q.w && k[0] == k[1];
   const uint32_t m = __ballot_sync(0xffffffffu, same8);
   if (same8) {
@@ -538,7 +544,7 @@ __global__ void __launch_bounds__(kP2Threads, 2) bucket_kernel(const uint16_t* _
             }
           }
 #pragma unroll
-          for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE>(s, q[u], vm[u], lane);
+          for (uint32_t u = 0; u < kP2Unroll; ++u) count_chunk<MODE, false>(s, q[u], vm[u], lane);
         }
       } else {
         // unbalanced (a few long segments among empty ones): number the 32 segments' chunks flat and let

@@ -6,7 +6,7 @@
 // sort by flipping the sign bit of the top digit.  Keys are only ever split
 // into digits; no two keys are compared by magnitude.
 //
-// GPU layout of one pass (one kernel, tiles of 8192 keys taken in ticket
+// GPU layout of one pass (one kernel, tiles of 16384 keys taken in ticket
 // order):
 //   * warp w of the CTA holds keys [512 w, 512 w + 512) of the tile, lane l
 //     key 32 i + l in step i, so the order (step, lane) is input order;
@@ -32,10 +32,10 @@
 namespace dialsort {
 namespace {
 
-constexpr uint32_t kRxThreads = 512;
+constexpr uint32_t kRxThreads = 1024;
 constexpr uint32_t kRxWarps = kRxThreads / 32;
 constexpr uint32_t kRxSteps = 16;                       // keys per thread
-constexpr uint32_t kRxTile = kRxThreads * kRxSteps;     // 8192 keys per tile
+constexpr uint32_t kRxTile = kRxThreads * kRxSteps;     // 16384 keys per tile
 constexpr uint32_t kRxDigits = 256;
 constexpr uint32_t kRxPasses = 4;
 
@@ -148,7 +148,7 @@ __device__ __forceinline__ uint32_t scan256(uint32_t v, uint32_t* red, uint32_t*
 }
 
 template <bool kSigned>
-__global__ void __launch_bounds__(kRxThreads, 2) rx_pass_kernel(const uint32_t* __restrict__ src,
+__global__ void __launch_bounds__(kRxThreads, 1) rx_pass_kernel(const uint32_t* __restrict__ src,
                                                                 uint32_t* __restrict__ dst, uint64_t n,
                                                                 uint32_t pass, uint64_t num_tiles,
                                                                 uint32_t* __restrict__ ghist,
@@ -389,7 +389,7 @@ dialsort_status_t radix_impl(const uint32_t* keys, uint64_t n, uint32_t* out, vo
 }  // namespace
 
 // Self-test of the bounded look-back wait: one CTA runs pass 0 on tile 1 of
-// 2^14 keys (the ticket starts at 1), so tile 0 never publishes and the wait
+// two tiles of keys (the ticket starts at 1), so tile 0 never publishes and the wait
 // for it runs out, recording ERRBIT_TIMEOUT.  Every write stays inside tmp.
 size_t radix_selftest_bytes() { return rx_layout(2 * kRxTile).total; }
 

@@ -30,9 +30,12 @@ def full_range(n, stream):
 def cases():
     yield "empty", np.zeros(0, dtype=np.uint32)
     yield "one", np.array([0xDEADBEEF], dtype=np.uint32)
-    yield "tile-1", full_range(8191, 9400)
-    yield "tile", full_range(8192, 9401)
-    yield "tile+1", full_range(8193, 9402)
+    yield "8191", full_range(8191, 9400)
+    yield "8193", full_range(8193, 9402)
+    yield "tile-1", full_range(16383, 9420)  # tiles of 16384 keys
+    yield "tile", full_range(16384, 9401)
+    yield "tile+1", full_range(16385, 9421)
+    yield "3tiles+5", full_range(3 * 16384 + 5, 9422)
     yield "ragged", full_range(1_000_003, 9403)
     yield "zipf-small", gen.keys(2_000_001, 1 << 20, "zipf", stream=9404)  # top two digits all zero
     yield "all-equal", np.full(300_001, 0x80000000, dtype=np.uint32)
