@@ -40,14 +40,20 @@ struct Item {
 
 // Pass-1 counters: one per (bucket, warp), bucket-major with a stride of
 // kP1Warps + 1 words, so one bucket's warp counters are contiguous for the
-// scan while one warp's buckets spread over all banks for the atomics.
+// scan while one warp's buckets spread over all banks for the atomics.  With
+// many buckets (B >= kCtaCounters) one counter per bucket for the whole CTA
+// instead: 16 columns of counters would crowd out CTAs, and the zeroing and
+// scan would grow with them.
 constexpr uint32_t kCntStride = kP1Warps + 1;
+constexpr uint32_t kCtaCounters = 256;
+__host__ __device__ __forceinline__ uint32_t p1_cols(uint32_t B) { return B >= kCtaCounters ? 1u : kP1Warps; }
+__host__ __device__ __forceinline__ uint32_t p1_stride(uint32_t B) { return B >= kCtaCounters ? 1u : kCntStride; }
 
 // Pass-1 shared memory, in 32-bit words: the tile's keys (filled by a bulk
 // copy), the staged low parts, the counters, the bucket totals, scan scratch
 // and the copy's mbarrier.
 __host__ __device__ __forceinline__ uint32_t p1_words(uint32_t B) {
-  return kP1Tile + kP1Tile / 2 + B * kCntStride + B + 32 + 2;
+  return kP1Tile + kP1Tile / 2 + B * p1_stride(B) + B + 32 + 2;
 }
 
 // Polls of a bulk copy's mbarrier before it is given up (each poll waits a while in hardware).
@@ -77,13 +83,15 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
   extern __shared__ __align__(128) uint32_t sm[];
   uint32_t* kbuf = sm;                                           // [8192] keys of the tile
   uint16_t* stage = reinterpret_cast<uint16_t*>(sm + kP1Tile);   // [8192] grouped low parts
-  uint32_t* cnt = sm + kP1Tile + kP1Tile / 2;                    // [B][kCntStride]: counts, then bases
-  uint32_t* bacc = cnt + B * kCntStride;                         // [B]: this CTA's bucket totals
+  const uint32_t cols = p1_cols(B), cstride = p1_stride(B);      // counters per bucket, and their stride
+  uint32_t* cnt = sm + kP1Tile + kP1Tile / 2;                    // [B][cstride]: counts, then bases
+  uint32_t* bacc = cnt + B * cstride;                            // [B]: this CTA's bucket totals
   uint32_t* red = bacc + B;                                      // [32] scan scratch; red[31]: stop flag
   uint64_t* bar = reinterpret_cast<uint64_t*>(red + 32);         // the key copy's mbarrier
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t lowmask = (1u << L) - 1u;
-  const uint32_t ncnt = B * kCntStride;
+  const uint32_t ncnt = B * cstride;
+  const uint32_t col = cols == 1u ? 0u : warp;  // this thread's counter column
   const uint64_t full_tiles = n / kP1Tile;  // tiles loaded by a bulk copy; the ragged last one by plain loads
   bool bad = false;
   uint32_t parity = 0;
@@ -150,13 +158,13 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     const uint32_t b0 = __shfl_sync(0xffffffffu, kv[0] >> L, 0);  // in every lane: no short circuit
     const bool one_bucket = __all_sync(0xffffffffu, vm == 0xffffu && same == 0xfffeu && (kv[0] >> L) == b0);
 
-    // ranks, two 16-bit ranks per register (a (bucket, warp) counter stays below 512)
+    // ranks, two 16-bit ranks per register (a counter stays below 8192)
     uint32_t rk[kP1Keys / 2];
 #pragma unroll
     for (uint32_t i = 0; i < kP1Keys / 2; ++i) rk[i] = 0;
     if (one_bucket) {
       uint32_t r0 = 0;
-      if (lane == 0) r0 = atomicAdd(cnt + b0 * kCntStride + warp, kP1Keys * 32u);
+      if (lane == 0) r0 = atomicAdd(cnt + b0 * cstride + col, kP1Keys * 32u);
       r0 = __shfl_sync(0xffffffffu, r0, 0) + lane;
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) rk[i / 2] |= (r0 + 32u * i) << (16 * (i & 1));
@@ -166,7 +174,7 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
       for (uint32_t i = 0; i < kP1Keys; ++i) {
         if ((vm >> i) & 1u) {
           if (!((same >> i) & 1u))  // a run starts here; its length counts the ones after it
-            r = atomicAdd(cnt + (kv[i] >> L) * kCntStride + warp, (uint32_t)__ffs(~(same >> (i + 1))));
+            r = atomicAdd(cnt + (kv[i] >> L) * cstride + col, (uint32_t)__ffs(~(same >> (i + 1))));
           else
             ++r;
         }
@@ -175,22 +183,22 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     } else if (vm == 0xffffu) {
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i)
-        rk[i / 2] |= atomicAdd(cnt + (kv[i] >> L) * kCntStride + warp, 1u) << (16 * (i & 1));
+        rk[i / 2] |= atomicAdd(cnt + (kv[i] >> L) * cstride + col, 1u) << (16 * (i & 1));
     } else {
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
-        const uint32_t r = ((vm >> i) & 1u) ? atomicAdd(cnt + (kv[i] >> L) * kCntStride + warp, 1u) : 0u;
+        const uint32_t r = ((vm >> i) & 1u) ? atomicAdd(cnt + (kv[i] >> L) * cstride + col, 1u) : 0u;
         rk[i / 2] |= r << (16 * (i & 1));
       }
     }
     __syncthreads();
 
     // bucket-major, warp-minor exclusive scan of the counts -> bases (in place)
-    const uint32_t E = kP1Warps * B;
+    const uint32_t E = cols * B;
     const uint32_t per = (E + kP1Threads - 1) / kP1Threads;
     const uint32_t e0 = min(tid * per, E), e1 = min(e0 + per, E);
     uint32_t local = 0;
-    for (uint32_t e = e0; e < e1; ++e) local += cnt[(e / kP1Warps) * kCntStride + e % kP1Warps];
+    for (uint32_t e = e0; e < e1; ++e) local += cnt[(e / cols) * cstride + e % cols];
     uint32_t x = local;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     __syncthreads();
     uint32_t acc = red[warp] + (x - local);
     for (uint32_t e = e0; e < e1; ++e) {
-      uint32_t* c = &cnt[(e / kP1Warps) * kCntStride + e % kP1Warps];
+      uint32_t* c = &cnt[(e / cols) * cstride + e % cols];
       const uint32_t v = *c;
       *c = acc;
       acc += v;
@@ -223,10 +231,10 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
     const uint32_t tile_valid = red[kP1Warps];
     uint16_t* trow = toff + t * (uint64_t)(B + 1);
     for (uint32_t b = tid; b <= B; b += kP1Threads) {
-      const uint32_t start = b < B ? cnt[b * kCntStride] : tile_valid;
+      const uint32_t start = b < B ? cnt[b * cstride] : tile_valid;
       trow[b] = (uint16_t)start;
       if (b < B) {
-        const uint32_t c = (b + 1 < B ? cnt[(b + 1) * kCntStride] : tile_valid) - start;
+        const uint32_t c = (b + 1 < B ? cnt[(b + 1) * cstride] : tile_valid) - start;
         bacc[b] += c;
         tcnt[(uint64_t)b * num_tiles + t] = (uint16_t)c;  // bucket-major copy for the split
       }
@@ -244,14 +252,14 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
         const uint32_t r = (rk[i / 2] >> (16 * (i & 1))) & 0xffffu;
-        stage[cnt[(kv[i] >> L) * kCntStride + warp] + r] = (uint16_t)(kv[i] & lowmask);
+        stage[cnt[(kv[i] >> L) * cstride + col] + r] = (uint16_t)(kv[i] & lowmask);
       }
     } else {
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {
         if ((vm >> i) & 1u) {
           const uint32_t r = (rk[i / 2] >> (16 * (i & 1))) & 0xffffu;
-          stage[cnt[(kv[i] >> L) * kCntStride + warp] + r] = (uint16_t)(kv[i] & lowmask);
+          stage[cnt[(kv[i] >> L) * cstride + col] + r] = (uint16_t)(kv[i] & lowmask);
         }
       }
     }
