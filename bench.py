@@ -177,6 +177,33 @@ def job_throughput(ms_local: float, keys_per_rank: int, steps: int, dist=None, d
     return world * keys_per_rank * steps / (ms / 1e3), ms
 
 
+def cpu_context(n_sample: int):
+    """Context lines on the host cores, on the same sample as the oracle baseline: the multi-threaded CPU
+    DialSort (per-thread histograms, bin-range expansion) on every core, and numpy's library sort."""
+    import gen
+    import cpu_baseline
+
+    keys = gen.keys(n_sample, UNIVERSE, DIST, stream=SEED_STREAM)
+    out = np.empty(n_sample, dtype=np.uint32)
+    cores = os.cpu_count() or 1
+
+    def best(fn, runs=5):
+        fn()
+        t = []
+        for _ in range(runs):
+            t0 = time.perf_counter()
+            fn()
+            t.append(time.perf_counter() - t0)
+        return n_sample / min(t)
+
+    par = best(lambda: cpu_baseline.sort(keys, UNIVERSE, out, cores))
+    lib = best(lambda: np.sort(keys), runs=3)
+    return {"parallel_cpu_dialsort": {"value": par, "unit": "keys/s", "cores": cores,
+                                      "how": "count into per-thread histograms, sum, expand bin ranges (OpenMP)"},
+            "library_sort": {"value": lib, "unit": "keys/s", "cores": 1, "how": "numpy.sort of the same keys"},
+            "sample": f"n={n_sample} keys uniform on [0,2^20)"}
+
+
 def _align(x, a):
     return (x + a - 1) // a * a
 
@@ -543,8 +570,10 @@ def main():
            "other_form": other}
 
     cpu = None
+    cpu_ctx = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, _ = cpu_baseline(1 << 25)
+        cpu_ctx = cpu_context(1 << 25)
 
     # the batched and served forms, each against per-request plain launches
     forms = {}
@@ -572,7 +601,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "whole_step_hbm": whole,
             "phases_ms": {"histogram": hist_ms, "offsets": offs_ms, "expand": expand_ms, "reconstruct": recon_ms},
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "cpu_baseline": cpu, "cpu_context": cpu_ctx, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches_per_step * args.steps, "step_stats": step_stats,
             "keys_per_sm_clock": value / world / (sms * 1e6 * (clk.summary()["sm_mhz"] or 2070.0)), "status": status, "hist_sum_ok": hist_sum_ok, "sorted_ok": sorted_ok,
         }
