@@ -20,7 +20,9 @@ def build(force: bool = False) -> str:
         return _LIB
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
     os.close(fd)
-    subprocess.run(["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC], check=True)
+    cmd = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC]
+    if subprocess.run(cmd[:3] + ["-fopenmp"] + cmd[3:], capture_output=True).returncode != 0:
+        subprocess.run(cmd, check=True)  # no OpenMP on this host: one thread
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -31,8 +33,15 @@ def _load():
         lib = ctypes.CDLL(build())
         lib.cpu_dialsort.restype = ctypes.c_int64
         lib.cpu_dialsort.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int]
+        lib.cpu_dialsort_threads.restype = ctypes.c_int
+        lib.cpu_dialsort_threads.argtypes = []
         _lib = lib
     return _lib
+
+
+def threads() -> int:
+    """Threads a call with threads=0 uses (1 when the host compiler has no OpenMP)."""
+    return _load().cpu_dialsort_threads()
 
 
 def sort(keys: np.ndarray, U: int, out: np.ndarray | None = None, threads: int = 0) -> np.ndarray:
