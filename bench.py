@@ -554,20 +554,69 @@ def main():
         v, _ = job_throughput(t, n, steps, dist, torch.device("cuda", local_rank))
         return v if steps else None
 
+    # Pipelined staged form: the same three operations per step, with consecutive steps overlapped on three
+    # streams (step i + 1's copy in runs during step i's sort and copy out; the two directions of the link
+    # carry data at the same time).  Inputs and outputs on the device are double-buffered.
+    d_in2 = [d_in, torch.empty_like(keys)]
+    d_out2 = [out, torch.empty_like(keys)]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def pipelined(steps):
+        done_sort, done_out = [], []
+        s_in.wait_stream(stream)
+        for i in range(steps):
+            j = i & 1
+            if i >= 2:
+                s_in.wait_event(done_sort[i - 2])  # the sort that read d_in2[j] has finished
+            with torch.cuda.stream(s_in):
+                d_in2[j].copy_(pin_in, non_blocking=True)
+            stream.wait_stream(s_in)
+            if i >= 2:
+                stream.wait_event(done_out[i - 2])  # d_out2[j] has been copied out
+            ds.sort(d_in2[j], U, out=d_out2[j], ws=ws, stream=stream)
+            ev_s = torch.cuda.Event()
+            ev_s.record(stream)
+            done_sort.append(ev_s)
+            s_out.wait_event(ev_s)
+            with torch.cuda.stream(s_out):
+                pin_out.copy_(d_out2[j], non_blocking=True)
+            ev_o = torch.cuda.Event()
+            ev_o.record(s_out)
+            done_out.append(ev_o)
+        stream.wait_stream(s_out)
+
+    def time_pipelined(steps):
+        if not steps:
+            return None
+        pipelined(2)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        pipelined(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v, _ = job_throughput(max(e0.elapsed_time(e1), 1e-9), n, steps, dist, torch.device("cuda", local_rank))
+        return v
+
     e2e_steps = min(args.e2e_steps, args.steps)
     e2e_value = time_e2e(e2e_step, e2e_steps)
     staged_value = time_e2e(staged_step, e2e_steps)
+    pipe_value = time_pipelined(e2e_steps)
     head = pin_out.numpy()[: 1 << 20].view(np.uint32 if w == 4 else np.uint16)
     e2e_ok = bool(np.all(head[1:] >= head[:-1])) if e2e_steps else None
     staged = {"value": staged_value, "how": "pinned host keys copied in (cudaMemcpyAsync), dialsort_sort on the "
               "device, sorted keys copied out; copies inside the timed region"}
     zero_copy = {"value": e2e_value, "how": "dialsort_sort given the pinned host buffers themselves: its kernels "
                  "read and write host memory across the CPU-GPU link"}
-    best, other = (staged, zero_copy) if (staged_value or 0) >= (e2e_value or 0) else (zero_copy, staged)
+    piped = {"value": pipe_value, "how": "copy in, dialsort_sort on the device, copy out, with consecutive steps "
+             "overlapped on three streams (double-buffered device input and output); every step's copies inside "
+             "the timed region"}
+    ranked = sorted([zero_copy, staged, piped], key=lambda f: f["value"] or 0, reverse=True)
+    best = ranked[0]
     e2e = {"value": best["value"], "unit": "keys/s",
            "h2d_bytes_per_step": w * n, "d2h_bytes_per_step": w * n, "steps": e2e_steps,
-           "host_output_sorted": e2e_ok, "how": best["how"] + " (the faster of two host-buffer forms)",
-           "other_form": other}
+           "host_output_sorted": e2e_ok, "how": best["how"] + " (the fastest of three host-buffer forms)",
+           "other_forms": ranked[1:]}
 
     cpu = None
     cpu_ctx = None
@@ -581,7 +630,7 @@ def main():
     # the batched and served forms, each against per-request plain launches
     forms = {}
     if not args.no_forms and n == N_KEYS:
-        del keys, out, ws, rws, pin_in, pin_out, d_in
+        del keys, out, ws, rws, pin_in, pin_out, d_in, d_in2, d_out2
         torch.cuda.empty_cache()
         forms["batched"] = run_batched(ds, torch, stream)
         torch.cuda.empty_cache()
