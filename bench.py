@@ -48,8 +48,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
     p.add_argument("--served-seconds", type=float, default=10.0)
-    p.add_argument("--form", default="all", choices=["all", "batched", "served", "radix"],
-                   help="print only the batched or served form's measurement")
+    p.add_argument("--form", default="all", choices=["all", "batched", "served", "radix", "paper"],
+                   help="print only one form's measurement (batched, served, radix, or the paper's workload grid)")
     # workload-size overrides, for profiling smaller cases of the same kernels
     p.add_argument("--n", type=int, default=N_KEYS)
     p.add_argument("--U", type=int, default=UNIVERSE)
@@ -236,6 +236,61 @@ def run_radix(ds, torch, stream, n: int = 1 << 28, steps: int = 20):
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "peak_source": peak_kind, "algorithmic_bytes_per_sort": 36 * n},
             "gpu_launches_per_sort": 5}
+
+
+PAPER_NS = (10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7)
+PAPER_US = (256, 1024, 65536)
+PAPER_DISTS = ("uniform", "paper_skew", "sorted", "reverse")
+
+
+def run_paper(ds, torch, stream, runs: int = 7, warm: int = 3):
+    """The paper's own workload grid (Sec. "Methodology"): N in {1e4, 1e5, 1e6, 1e7} x U in {256, 1024,
+    65536} x {uniform, skewed (80 % of keys in [0, 0.05 U]), sorted, reverse}, each sorted by dialsort_sort
+    `runs` times after `warm` warm-ups (the paper's best-of-7 protocol, with mean and CV), plus
+    DialSort-Radix on 1e7 full-range int32 keys.  Inputs of these sizes stay in L2, and the small ones
+    are bound by launch latency, so these are context lines beside the paper's CPU figures, not roofline
+    figures."""
+    import gen
+
+    def timed(fn):
+        for _ in range(warm):
+            fn()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(runs + 1)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for i in range(runs):
+            fn()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        return np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(runs)])
+
+    rows = []
+    sid = 12 * 16
+    for N in PAPER_NS:
+        for U in PAPER_US:
+            for dist in PAPER_DISTS:
+                sid += 1
+                keys = torch.from_numpy(gen.keys(N, U, dist, stream=sid).view(np.int32)).cuda()
+                out = torch.empty_like(keys)
+                ws = torch.empty(ds.sort_workspace_size(N, U), dtype=torch.uint8, device="cuda")
+                t = timed(lambda: ds.sort(keys, U, out=out, ws=ws, stream=stream))
+                ok = bool(torch.all(out[1:] >= out[:-1]).item())
+                rows.append({"N": N, "U": U, "dist": dist, "best_ms": float(t.min()), "mean_ms": float(t.mean()),
+                             "cv": float(t.std() / t.mean()), "keys_per_s_best": N / (float(t.min()) / 1e3),
+                             "sorted_ok": ok})
+    n_rx = 10 ** 7
+    words = torch.from_numpy(gen.words(n_rx, stream=sid + 1).astype(np.uint32).view(np.int32)).cuda()
+    rx_out = torch.empty_like(words)
+    rx_ws = torch.empty(ds.lib().dialsort_radix_workspace_size(n_rx), dtype=torch.uint8, device="cuda")
+    t = timed(lambda: ds.radix_sort(words, out=rx_out, ws=rx_ws, stream=stream))
+    radix = {"N": n_rx, "best_ms": float(t.min()), "mean_ms": float(t.mean()), "cv": float(t.std() / t.mean()),
+             "keys_per_s_best": n_rx / (float(t.min()) / 1e3),
+             "sorted_ok": bool(torch.all(rx_out[1:] >= rx_out[:-1]).item())}
+    return {"workload": "the paper's grid: dialsort_sort of N uint32 keys, N in {1e4,1e5,1e6,1e7}, U in "
+                        "{256,1024,65536}, uniform / skewed / sorted / reverse; DialSort-Radix on 1e7 int32",
+            "protocol": f"{warm} warm-ups, best / mean / CV of {runs} runs (CUDA events per run)",
+            "l2": "inputs smaller than L2 (context, not roofline)", "rows": rows, "radix": radix,
+            "status": ds.stream_status()}
 
 
 def run_batched(ds, torch, stream, reps: int = 3):
@@ -430,6 +485,8 @@ def main():
             res = run_batched(ds, torch, stream)
         elif args.form == "radix":
             res = run_radix(ds, torch, stream, n=args.n)
+        elif args.form == "paper":
+            res = run_paper(ds, torch, stream)
         else:
             res = run_served(ds, torch, seconds=args.served_seconds)
         print(json.dumps({"form": args.form, **res}), flush=True)
@@ -637,6 +694,11 @@ def main():
         forms["served"] = run_served(ds, torch, seconds=args.served_seconds)
         torch.cuda.empty_cache()
         forms["radix"] = run_radix(ds, torch, stream)
+        torch.cuda.empty_cache()
+        try:  # context lines only: never fails the benchmark
+            forms["paper_grid"] = run_paper(ds, torch, stream)
+        except Exception as exc:
+            forms["paper_grid"] = {"unavailable": str(exc)[:200]}
         torch.cuda.empty_cache()
 
     if rank == 0:
