@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
     p.add_argument("--served-seconds", type=float, default=10.0)
+    p.add_argument("--reference-seconds", type=float, default=60.0,
+                   help="host time the reference arm (the oracle) spends on its timed and warm-up steps")
     p.add_argument("--form", default="all", choices=["all", "batched", "served", "radix", "paper"],
                    help="print only one form's measurement (batched, served, radix, or the paper's workload grid)")
     # workload-size overrides, for profiling smaller cases of the same kernels
@@ -439,12 +441,12 @@ def run_reference(args, rank, world):
     import gen
     import oracle
 
-    # calibrate a per-step sample so that all steps finish in about a minute
+    # calibrate a per-step sample so that all steps finish in about --reference-seconds (a minute)
     cal = gen.keys(1 << 20, UNIVERSE, DIST, stream=SEED_STREAM)
     t0 = time.perf_counter()
     oracle.sort(cal, UNIVERSE)
     rate = (1 << 20) / max(time.perf_counter() - t0, 1e-6)
-    per_step = 60.0 / max(1, args.steps + args.warmup)
+    per_step = args.reference_seconds / max(1, args.steps + args.warmup)
     n_s = int(min(N_KEYS, max(1 << 16, rate * per_step)))
     keys = gen.keys(n_s, UNIVERSE, DIST, stream=SEED_STREAM)
     for _ in range(args.warmup):
