@@ -12,6 +12,9 @@ K, H, OUT, WS = 4096, 8192, 12288, 16384  # 256-byte aligned fake device address
 
 @pytest.fixture(scope="module")
 def lib():
+    import __graft_entry__ as g
+
+    g.build()
     import paper_2605_16667_gb300 as ds
 
     return ds.lib()

@@ -11,6 +11,9 @@ US = [1, 2, 255, 256, 1024, 4096, 65536, 65537, 1 << 20, (1 << 20) + 1, 1 << 24,
 
 @pytest.fixture(scope="module")
 def lib():
+    import __graft_entry__ as g
+
+    g.build()
     import paper_2605_16667_gb300 as ds
 
     return ds.lib()
