@@ -89,6 +89,7 @@ dialsort_status_t check_keys(const void* keys, uint32_t key_bytes, uint64_t n, u
 
 size_t hist_ws_bytes(uint64_t n, uint32_t U, uint32_t key_bytes) {
   if (key_bytes != 4 || n < (1u << 20)) return 0;
+  if (hier_shape_fits(n, U, key_bytes)) return hier_layout(n, U).total;
   return two_level_layout(n, U).total;
 }
 
@@ -115,8 +116,13 @@ dialsort_status_t histogram_impl(const void* keys, uint32_t key_bytes, uint64_t 
   const bool forced = plan.regime == DIALSORT_REGIME_TWO_LEVEL;
   const bool auto_large = (cfg == nullptr || cfg->regime == DIALSORT_REGIME_AUTO) &&
                           (plan.regime == DIALSORT_REGIME_GLOBAL_CRN || plan.regime == DIALSORT_REGIME_GLOBAL);
-  // the two-level pass 1 moves keys with bulk (TMA) copies from device memory
-  if ((forced || auto_large) && !keys_in_host && two_level_fits(n, U, key_bytes, keys)) {
+  // the two-level passes read device memory (the U > 2^21 form moves keys with bulk (TMA) copies)
+  if ((forced || auto_large) && !keys_in_host && hier_fits(n, U, key_bytes, keys)) {
+    const HierLayout T = hier_layout(n, U);
+    if (ws != nullptr && ws_bytes >= T.total)
+      return from_cuda(launch_hier(static_cast<const uint32_t*>(keys), n, U, H, ws, T, *dev, dev->err, st, accumulate));
+    if (forced) return DIALSORT_ERR_WORKSPACE;
+  } else if ((forced || auto_large) && !keys_in_host && two_level_fits(n, U, key_bytes, keys)) {
     const TwoLevelLayout T = two_level_layout(n, U);
     if (ws != nullptr && ws_bytes >= T.total)
       return from_cuda(launch_two_level(static_cast<const uint32_t*>(keys), n, U, H, ws, T, plan.crn, *dev,
@@ -280,7 +286,7 @@ dialsort_status_t dialsort_plan_histogram(uint64_t n, uint32_t U, uint32_t key_b
   // what dialsort_histogram_ws does with aligned keys and a large enough workspace
   if (in.regime == DIALSORT_REGIME_AUTO &&
       (regime == DIALSORT_REGIME_GLOBAL_CRN || regime == DIALSORT_REGIME_GLOBAL) &&
-      two_level_shape_fits(n, U, key_bytes))
+      (hier_shape_fits(n, U, key_bytes) || two_level_shape_fits(n, U, key_bytes)))
     regime = DIALSORT_REGIME_TWO_LEVEL;
   *cfg = dialsort_hist_config_t{regime, crn_cfg, p.blocks, p.threads, p.replicas, p.cluster};
   return DIALSORT_OK;

@@ -106,6 +106,15 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
+// Shared -> global bulk reduce-add of 32-bit words (16-byte aligned, bytes a multiple of 16), in a bulk group:
+// the L2 adds src into dst.
+__device__ __forceinline__ void bulk_reduce_add_u32(uint32_t* dst, const uint32_t* src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
 // Thread 0: wait until every committed bulk store has finished reading shared memory.
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 

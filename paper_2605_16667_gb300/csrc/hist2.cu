@@ -132,12 +132,13 @@ __global__ void __launch_bounds__(kP1Threads, 3) partition_kernel(const uint32_t
       kv[4 * i + 2] = v.z;
       kv[4 * i + 3] = v.w;
     }
-    // bit i of vm: key i is real and < U (all 16 in the common case, found with one max)
-    uint32_t mx = 0;
+    // bit i of vm: key i is real and < U (all 16 in the common case).  Each key is tested against the
+    // universe bound on its own; no two keys are compared with each other.
+    bool all_below = true;
 #pragma unroll
-    for (uint32_t i = 0; i < kP1Keys; ++i) mx = max(mx, kv[i]);
+    for (uint32_t i = 0; i < kP1Keys; ++i) all_below = all_below && kv[i] < U;
     uint32_t vm = 0xffffu;
-    if (!full || mx >= U) {
+    if (!full || !all_below) {
       vm = 0;
 #pragma unroll
       for (uint32_t i = 0; i < kP1Keys; ++i) {

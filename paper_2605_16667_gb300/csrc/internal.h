@@ -66,6 +66,24 @@ cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint3
                              const TwoLevelLayout& T, uint32_t crn_mode, const DeviceInfo& dev, uint32_t* err,
                              cudaStream_t stream, bool accumulate);
 
+// Two-level ingestion with per-(bucket, lane) partition counters for 2^16 < U <= 2^21.  hier.cu
+struct HierLayout {
+  uint32_t B = 0, BM = 0;        // buckets of 2^15 bins; bucket slots of the partition kernel (32 or 64)
+  uint64_t num_tiles = 0;        // 8192-key tiles
+  uint32_t S_t = 0;              // staged entries per tile in the workspace
+  uint32_t G_max = 0;            // pass-2 CTAs the scratch has room for
+  size_t off_low = 0, off_seg = 0, off_btot = 0, off_start = 0, off_used = 0, off_part = 0;
+  size_t total = 0;
+};
+constexpr uint32_t kHierMaxCountCtas = 256;  // pass-2 CTAs (one per SM) at most
+// Pass-2 CTAs for n keys on a GPU with `sms` SMs (no more than the workspace has room for).
+uint32_t hier_count_ctas(uint64_t n, uint32_t sms);
+HierLayout hier_layout(uint64_t n, uint32_t U);
+bool hier_shape_fits(uint64_t n, uint32_t U, uint32_t key_bytes);
+bool hier_fits(uint64_t n, uint32_t U, uint32_t key_bytes, const void* keys);
+cudaError_t launch_hier(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* ws, const HierLayout& T,
+                        const DeviceInfo& dev, uint32_t* err, cudaStream_t stream, bool accumulate);
+
 // Self-tests of the bounded device waits (a wait that is made to run out).
 size_t offsets_selftest_bytes();
 cudaError_t launch_offsets_selftest(void* ws, uint32_t* err, cudaStream_t stream);
