@@ -351,8 +351,10 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_count_kernel(
     uint32_t* __restrict__ H, uint32_t* __restrict__ part, uint32_t* __restrict__ part_used) {
   extern __shared__ __align__(128) uint32_t hist[];  // 2^15 bins
   __shared__ uint32_t wred[kP2Threads / 32];
-  __shared__ uint32_t pre[kP2Threads + 1];  // first chunk of each segment of the current window
-  __shared__ uint32_t sw[kP2Threads];       // the window's segment words
+  __shared__ uint32_t cpre[kP2Threads + 2];  // first chunk of each non-empty segment of the window, then
+                                             // the window's chunk count and a sentinel
+  __shared__ uint32_t csw[kP2Threads];       // their segment words
+  __shared__ uint16_t ctile[kP2Threads];     // their tiles, relative to the window
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   constexpr uint32_t bins = 1u << kLow;
   uint64_t s = start[blockIdx.x];
@@ -374,13 +376,17 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_count_kernel(
     const uint32_t hb_a = smem_addr(hist) - ((b & 1u) << kLow) * 4u;
     const uint32_t* row = seg + (uint64_t)b * num_tiles;
     uint32_t rkey = 0, rcnt = 0;
-    // windows of up to 1024 tiles: a block scan numbers the window's chunks (16-byte pieces of the
-    // segments) flat, and every warp takes an equal contiguous range of them
+    // Windows of up to 1024 tiles.  One block scan numbers the window's non-empty segments and their
+    // chunks (16-byte pieces, 8 low parts each) flat; every warp then takes an equal contiguous range of
+    // chunks.  Within a warp step lane l takes chunk j0 + l: the segment boundaries falling inside the
+    // step are gathered into a 32-bit mask (one boundary per lane, redux.or), and a popcount of the
+    // mask below bit l gives the lane's segment.
     for (uint64_t w0 = ta; w0 < tb; w0 += kP2Threads) {
       const uint32_t nw = (uint32_t)min((uint64_t)kP2Threads, tb - w0);
       const uint32_t sgw = tid < nw ? row[w0 + tid] : 0u;
       const uint32_t ch = ((sgw >> 16) + 7u) >> 3;
-      uint32_t x = ch;
+      const uint32_t packed = (ch << 11) | (ch ? 1u : 0u);  // chunks (21 bits) | non-empty segments (11 bits)
+      uint32_t x = packed;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
@@ -388,7 +394,6 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_count_kernel(
       }
       __syncthreads();  // the previous window's tables are no longer read
       if (lane == 31) wred[warp] = x;
-      sw[tid] = sgw;
       __syncthreads();
       uint32_t wbase = 0, total = 0;
       for (uint32_t w = 0; w < kP2Threads / 32; ++w) {
@@ -396,40 +401,45 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_count_kernel(
         if (w < warp) wbase += v;
         total += v;
       }
-      pre[tid] = wbase + x - ch;  // first chunk of entry tid
-      if (tid == 0) pre[kP2Threads] = total;
+      const uint32_t excl = wbase + x - packed;
+      if (ch) {
+        const uint32_t i = excl & 0x7ffu;
+        cpre[i] = excl >> 11;
+        csw[i] = sgw;
+        ctile[i] = (uint16_t)tid;
+      }
+      const uint32_t nnz = total & 0x7ffu, nch = total >> 11;
+      if (tid == 0) cpre[nnz] = nch;
+      if (tid == 1) cpre[nnz + 1] = 0xffffffffu;  // sentinel past the last boundary
       __syncthreads();
-      const uint32_t j_lo = (uint32_t)((uint64_t)total * warp / (kP2Threads / 32));
-      const uint32_t j_hi = (uint32_t)((uint64_t)total * (warp + 1) / (kP2Threads / 32));
+      const uint32_t j_lo = (uint32_t)((uint64_t)nch * warp / (kP2Threads / 32));
+      const uint32_t j_hi = (uint32_t)((uint64_t)nch * (warp + 1) / (kP2Threads / 32));
       if (j_lo >= j_hi) continue;
-      // the entry holding chunk j_lo: the last e with pre[e] <= j_lo (binary search, same in every lane)
+      // the segment holding chunk j_lo: the last e with cpre[e] <= j_lo (same in every lane)
       uint32_t e = 0;
       for (uint32_t step = kP2Threads / 2; step != 0; step >>= 1)
-        if (e + step < nw && pre[e + step] <= j_lo) e += step;
-      constexpr int F = 2;  // chunks in flight per lane
+        if (e + step < nnz && cpre[e + step] <= j_lo) e += step;
+      constexpr int F = 4;  // chunks in flight per lane
       for (uint32_t j0 = j_lo; j0 < j_hi; j0 += 32u * F) {  // warp-uniform bound
         uint4 q[F];
         uint32_t nh[F];
 #pragma unroll
         for (int f = 0; f < F; ++f) {
-          const uint32_t j = j0 + 32u * f + lane;
-          const bool live = j < j_hi;
-          // walk from the warp's entry to this lane's (empty segments are passed over)
-          uint32_t idx = e;
-          while (__any_sync(0xffffffffu, live && pre[idx + 1] <= j)) {
-            if (live && pre[idx + 1] <= j) ++idx;
-          }
+          const uint32_t jf = j0 + 32u * f, j = jf + lane;
+          // boundaries cpre[e + 1 + k] (k = lane) inside [jf, jf + 32) -> mask bits; cpre[e + 1] >= jf
+          const uint32_t bk = cpre[min(e + 1u + lane, nnz + 1u)] - jf;
+          const uint32_t m = __reduce_or_sync(0xffffffffu, bk < 32u ? 1u << bk : 0u);
+          const uint32_t idx = e + __popc(m & (0xffffffffu >> (31u - lane)));
+          e = __shfl_sync(0xffffffffu, idx, 31);
           q[f] = make_uint4(0u, 0u, 0u, 0u);
           nh[f] = 0;
-          if (live) {
-            const uint32_t sgu = sw[idx], c = j - pre[idx], cnt = sgu >> 16;
+          if (j < j_hi) {
+            const uint32_t sgu = csw[idx], c = j - cpre[idx], cnt = sgu >> 16;
             nh[f] = cnt - c * 8u >= 8u ? 8u : cnt - c * 8u;
-            q[f] = ld_stream_v4(reinterpret_cast<const uint4*>(low + (w0 + idx) * (uint64_t)S_t + (sgu & 0xffffu) * 8u) + c);
+            q[f] = ld_stream_v4(
+                reinterpret_cast<const uint4*>(low + (w0 + ctile[idx]) * (uint64_t)S_t + (sgu & 0xffffu) * 8u) + c);
           }
-          e = __shfl_sync(0xffffffffu, idx, 0);  // lane 0 holds the lowest chunk; later lanes start at or after it
-          if (f + 1 < F) e = __shfl_sync(0xffffffffu, idx, 31) < e ? e : __shfl_sync(0xffffffffu, idx, 31);
         }
-        e = __shfl_sync(0xffffffffu, e, 0);
 #pragma unroll
         for (int f = 0; f < F; ++f) {
           const uint4 w = q[f];
