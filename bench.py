@@ -96,37 +96,62 @@ def ncu_traffic(phase: str):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples while the timed region runs."""
+    """nvidia-smi clock and throttle-reason samples (every 10 ms) around the timed region.
+
+    The sampler starts before the region and waits for its first line, so the region is covered from
+    its start; `mark(True/False)` brackets the timed region, and `summary()` reports the samples taken
+    inside it.  A short timed region (a few sorts of about a millisecond) still holds few samples, so
+    the caller keeps the GPU busy with the same sort for a while after the region (`soak`), and those
+    samples are reported beside the region's own ("soak_samples")."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 10):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
+        self.lines = []  # (time, line)
+        self.window = [None, None]
+        self.soak = [None, None]
+
+    def _reader(self):
+        import time
+        for line in self.proc.stdout:
+            self.lines.append((time.monotonic(), line))
 
     def __enter__(self):
+        import threading
+        import time
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._reader, daemon=True).start()
+            t0 = time.monotonic()
+            while not self.lines and time.monotonic() - t0 < 3.0:  # sampling must be live before the region
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
+    def mark(self, which: str, start: bool):
+        import time
+        (self.window if which == "region" else self.soak)[0 if start else 1] = time.monotonic()
+
     def __exit__(self, *exc):
-        self.out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    @staticmethod
+    def _parse(lines):
         sm, mx, reasons = [], None, set()
-        for line in (self.out or "").splitlines():
+        for _, line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -139,8 +164,20 @@ class ClockSampler:
             for name, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(name)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return sm, mx, reasons
+
+    def summary(self):
+        def within(w):
+            if w[0] is None:
+                return []
+            end = w[1] if w[1] is not None else float("inf")
+            return [(t, l) for t, l in self.lines if w[0] <= t <= end]
+        sm, mx, reasons = self._parse(within(self.window))
+        ssm, smx, sreasons = self._parse(within(self.soak))
+        allsm = sm + ssm
+        return {"sm_mhz": float(np.median(allsm)) if allsm else None, "sm_max_mhz": mx or smx,
+                "reasons": sorted(reasons | sreasons), "samples": len(sm), "soak_samples": len(ssm),
+                "period_ms": self.period_ms}
 
 
 def cpu_baseline(n_sample: int, runs_budget_s: float = 15.0):
@@ -231,13 +268,22 @@ def run_radix(ds, torch, stream, n: int = 1 << 28, steps: int = 20):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
-    ok = bool(torch.all(out[1:] >= out[:-1]).item()) and ds.stream_status() == ds.OK
+    ok = matches_library_sort(torch, keys, out) and ds.stream_status() == ds.OK
     gbs = 36 * n / (ms / 1e3) / 1e9
     return {"workload": f"dialsort_radix_sort_i32 n={n} full-range int32 (uniform 32-bit words)",
             "value": n / (ms / 1e3), "unit": "keys/s", "ms_per_sort": ms, "sorted_ok": ok,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "peak_source": peak_kind, "algorithmic_bytes_per_sort": 36 * n},
             "gpu_launches_per_sort": 5}
+
+
+def matches_library_sort(torch, keys, out) -> bool:
+    """The output is the input's multiset in order: equal, element by element, to torch's own sort of the
+    input (a check outside every timed region; int32 order equals uint32 order for keys below 2^31, and
+    16-bit keys are compared as unsigned values)."""
+    if keys.dtype == torch.int16:
+        keys, out = keys.to(torch.int32) & 0xFFFF, out.to(torch.int32) & 0xFFFF
+    return bool(torch.equal(torch.sort(keys.flatten()).values, out.flatten()))
 
 
 PAPER_NS = (10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7)
@@ -276,7 +322,7 @@ def run_paper(ds, torch, stream, runs: int = 7, warm: int = 3):
                 out = torch.empty_like(keys)
                 ws = torch.empty(ds.sort_workspace_size(N, U), dtype=torch.uint8, device="cuda")
                 t = timed(lambda: ds.sort(keys, U, out=out, ws=ws, stream=stream))
-                ok = bool(torch.all(out[1:] >= out[:-1]).item())
+                ok = matches_library_sort(torch, keys, out)
                 rows.append({"N": N, "U": U, "dist": dist, "best_ms": float(t.min()), "mean_ms": float(t.mean()),
                              "cv": float(t.std() / t.mean()), "keys_per_s_best": N / (float(t.min()) / 1e3),
                              "sorted_ok": ok})
@@ -287,7 +333,7 @@ def run_paper(ds, torch, stream, runs: int = 7, warm: int = 3):
     t = timed(lambda: ds.radix_sort(words, out=rx_out, ws=rx_ws, stream=stream))
     radix = {"N": n_rx, "best_ms": float(t.min()), "mean_ms": float(t.mean()), "cv": float(t.std() / t.mean()),
              "keys_per_s_best": n_rx / (float(t.min()) / 1e3),
-             "sorted_ok": bool(torch.all(rx_out[1:] >= rx_out[:-1]).item())}
+             "sorted_ok": matches_library_sort(torch, words, rx_out)}
     return {"workload": "the paper's grid: dialsort_sort of N uint32 keys, N in {1e4,1e5,1e6,1e7}, U in "
                         "{256,1024,65536}, uniform / skewed / sorted / reverse; DialSort-Radix on 1e7 int32",
             "protocol": f"{warm} warm-ups, best / mean / CV of {runs} runs (CUDA events per run)",
@@ -531,11 +577,21 @@ def main():
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
+        clk.mark("region", True)
         e0.record(stream)
         for i in range(args.steps):
             step()
             ev[i + 1].record(stream)
         torch.cuda.synchronize()
+        clk.mark("region", False)
+        # the same sort for about 0.3 s more (untimed), so that the clock record holds enough samples
+        clk.mark("soak", True)
+        t_soak = time.monotonic()
+        while time.monotonic() - t_soak < 0.3:
+            for _ in range(16):
+                step()
+            torch.cuda.synchronize()
+        clk.mark("soak", False)
     barrier()
     ms = e0.elapsed_time(e1)
     per_step = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)])
@@ -543,8 +599,8 @@ def main():
                   "std_ms": float(per_step.std()), "cv": float(per_step.std() / per_step.mean())}
     value, ms = job_throughput(ms, n, args.steps, dist, torch.device("cuda", local_rank))
 
-    # sanity on the last result (outside the timed region): sorted, sum(H) = n
-    sorted_ok = bool(torch.all(out[1:] >= out[:-1]).item())
+    # sanity on the last result (outside the timed region): the input's multiset in order, sum(H) = n
+    sorted_ok = matches_library_sort(torch, keys, out)
     Hs = ws[: 4 * U].view(torch.int32)
     hist_sum_ok = int(Hs.to(torch.int64).sum().item()) == n
     status = ds.stream_status()

@@ -21,8 +21,6 @@ std::once_flag g_once[kMaxDevices];
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-dialsort_status_t from_cuda(cudaError_t e) { return e == cudaSuccess ? DIALSORT_OK : DIALSORT_ERR_CUDA; }
-
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 }  // namespace

@@ -110,4 +110,7 @@ cudaError_t launch_expand(const uint32_t* H, uint32_t U, uint64_t n, void* out, 
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// The status every entry point returns for a CUDA runtime result.
+inline dialsort_status_t from_cuda(cudaError_t e) { return e == cudaSuccess ? DIALSORT_OK : DIALSORT_ERR_CUDA; }
+
 }  // namespace dialsort

@@ -13,9 +13,11 @@
 // kernel handed it would fault or, where the GPU can reach host memory,
 // silently use the wrong memory.  So, once per device and with that device
 // current, the first call looks up the array's device address with
-// cudaGetSymbolAddress, checks the result, and caches it; every launch gets
-// that address.  The first call on a device should therefore come before any
-// stream capture.
+// cudaGetSymbolAddress, checks the result, and caches it (a failed look-up is
+// not cached: the next call retries); every launch gets that address.  The
+// first call on a device should therefore come before any stream capture.
+// H and out are checked like dialsort_reconstruct's: device memory of the
+// current device, or host memory the device can reach.
 //
 // Every call on a device shares the one array, which keeps the previous
 // call's contents.  The parts that must start at zero (the tile ticket and the
@@ -35,19 +37,27 @@ constexpr size_t kNoallocScratchBytes = DIALSORT_NOALLOC_SCRATCH_BYTES;  // per 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDev = 64;
-void* g_scratch_ptr[kMaxDev];
-cudaError_t g_scratch_err[kMaxDev];
-std::once_flag g_scratch_once[kMaxDev];
+void* g_scratch_ptr[kMaxDev];  // cached device addresses; only successful look-ups are kept
+std::mutex g_scratch_mu;
 
-// Device address of this device's scratch array, looked up once per device.
+// Device address of this device's scratch array.  A failed look-up (for
+// example one made while a stream is being captured) is not cached: its
+// error is cleared and the next call tries again.
 cudaError_t scratch_address(int dev, void** ptr) {
-  std::call_once(g_scratch_once[dev], [dev] {
+  *ptr = nullptr;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (g_scratch_ptr[dev] == nullptr) {
     void* p = nullptr;
-    g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    g_scratch_ptr[dev] = (g_scratch_err[dev] == cudaSuccess) ? p : nullptr;
-  });
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      (void)cudaGetLastError();  // leave no sticky error behind for the caller's next CUDA call
+      return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    }
+    g_scratch_ptr[dev] = p;
+  }
   *ptr = g_scratch_ptr[dev];
-  return g_scratch_err[dev];
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -64,10 +74,19 @@ extern "C" dialsort_status_t dialsort_reconstruct_noalloc(const uint32_t* H, uin
   if (L.total > kNoallocScratchBytes) return DIALSORT_ERR_WORKSPACE;  // beyond the fixed scratch
   const DeviceInfo* dev = device_info();
   if (!dev) return DIALSORT_ERR_CUDA;
+  // H and out are classified exactly as dialsort_reconstruct classifies them: memory of another
+  // device, or host memory this device cannot reach, is refused before any launch
+  const void* hp;
+  const void* op;
+  dialsort_status_t s = kernel_address(H, *dev, &hp);
+  if (s == DIALSORT_OK) s = kernel_address(n ? out : nullptr, *dev, &op);
+  if (s != DIALSORT_OK) return s;
   void* scratch = nullptr;
-  if (scratch_address(dev->device, &scratch) != cudaSuccess || scratch == nullptr) return DIALSORT_ERR_CUDA;
+  if (scratch_address(dev->device, &scratch) != cudaSuccess) return DIALSORT_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = launch_offsets(H, U, n, scratch, L, dev->err, st);  // clears ticket + descriptors first
-  if (e == cudaSuccess) e = launch_expand(H, U, n, out, 4, scratch, L, st);
-  return e == cudaSuccess ? DIALSORT_OK : DIALSORT_ERR_CUDA;
+  const uint32_t* Hk = static_cast<const uint32_t*>(hp);
+  void* outk = n ? const_cast<void*>(op) : static_cast<void*>(out);
+  cudaError_t e = launch_offsets(Hk, U, n, scratch, L, dev->err, st);  // clears ticket + descriptors first
+  if (e == cudaSuccess) e = launch_expand(Hk, U, n, outk, 4, scratch, L, st);
+  return from_cuda(e);
 }

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 import gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -73,6 +74,53 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls_in_a_row(ds):
     b = _noalloc_projection(ds, H, 4099, 123_457)
     torch.cuda.synchronize()
     assert torch.equal(a, want) and torch.equal(b, want)
+
+
+def test_noalloc_matches_the_oracle_and_allocates_nothing(ds):
+    n, U = (1 << 19) + 5, 1 << 14
+    keys = gen.keys(n, U, "zipf", stream=44)
+    H = ds.histogram(torch.from_numpy(keys.view(np.int32)).cuda(), U)
+    first = _noalloc_projection(ds, H, U, n)  # the first call on a device looks up the scratch address
+    torch.cuda.synchronize()
+    # the direct check: the CPU oracle's projection of the same histogram, element by element
+    want = oracle.reconstruct(H.cpu().numpy().view(np.uint32), U)
+    assert np.array_equal(first.cpu().numpy().view(np.uint32), want)
+    # the property the entry point exists for: a further call takes no device memory
+    out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    st = ds.lib().dialsort_reconstruct_noalloc(H.data_ptr(), U, out.data_ptr(), n,
+                                               torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free_after = torch.cuda.mem_get_info()[0]
+    assert st == ds.OK and free_after == free_before
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), want)
+
+
+def test_noalloc_classifies_h_and_out_like_the_workspace_entry_point(ds):
+    """A histogram in plain (pageable) host memory: refused where the GPU cannot read host page
+    tables, read across the CPU-GPU link where it can -- exactly as dialsort_reconstruct does."""
+    n, U = 4099, 256
+    keys = gen.keys(n, U, "uniform", stream=45)
+    buf = np.zeros(U + 4, np.uint32)  # a 16-byte aligned view into plain host memory
+    off = (-buf.ctypes.data % 16) // 4
+    H_host = buf[off:off + U]
+    H_host[:] = oracle.histogram(keys, U)[0]
+    out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    L = ds.lib()
+    st = L.dialsort_reconstruct_noalloc(H_host.ctypes.data, U, out.data_ptr(), n, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    ws = torch.empty(ds.reconstruct_workspace_size(U, n), dtype=torch.uint8, device="cuda")
+    out2 = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    st2 = L.dialsort_reconstruct(H_host.ctypes.data, U, out2.data_ptr(), n, ws.data_ptr(), ws.numel(),
+                                 torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert st == st2
+    if L.dialsort_pageable_host_access() == 1:
+        assert st == ds.OK
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.reconstruct(H_host, U))
+    else:
+        assert st == ds.ERR_INVALID_ARG
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch(ds):
