@@ -352,10 +352,7 @@ def run_batched(ds, torch, stream, reps: int = 3):
     import gen
 
     count = 4096
-    ns = gen.loguniform(count, 10, 22, stream=4 * 16).astype(np.int64)
-    us = gen.loguniform(count, 8, 20, stream=4 * 16 + 1).astype(np.int64)
-    picks = gen.words(count, stream=4 * 16 + 2)
-    dists = [["uniform", "zipf", "all_equal"][int(p % 3)] for p in picks]
+    ns, us, dists = gen.batch_workload(count)
     koff = np.zeros(count + 1, dtype=np.int64)
     hoff = np.zeros(count + 1, dtype=np.int64)
     for i in range(count):
@@ -364,8 +361,7 @@ def run_batched(ds, torch, stream, reps: int = 3):
     host = np.empty(int(koff[-1]), dtype=np.uint32)
 
     def fill(i):
-        gen.keys(int(ns[i]), int(us[i]), dists[i], stream=4 * 16 * 1000 + i,
-                 out=host[koff[i]:koff[i] + ns[i]])
+        gen.batch_keys(i, ns[i], us[i], dists[i], out=host[koff[i]:koff[i] + ns[i]])
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         list(ex.map(fill, range(count)))
@@ -382,7 +378,10 @@ def run_batched(ds, torch, stream, reps: int = 3):
     b.launch(stream)
     torch.cuda.synchronize()
     ok = ds.stream_status() == ds.OK
-    # spot-check a few instances against numpy sort (outside any timing)
+    # every instance against the same instance through the single-instance entry points (outside any
+    # timing; the full comparison with the CPU oracle is tests/test_gpu_fullsize.py)
+    for i in range(count):
+        ok = ok and torch.equal(hv[i], ds.histogram(kv[i], int(us[i]))) and torch.equal(ov[i], ds.sort(kv[i], int(us[i])))
     for i in (0, count // 2, count - 1):
         ok = ok and bool(np.array_equal(ov[i].cpu().numpy().view(np.uint32), np.sort(host[koff[i]:koff[i] + ns[i]])))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -419,7 +418,9 @@ def run_batched(ds, torch, stream, reps: int = 3):
             "plain_launches_ms": plain_ms, "batched_keys_per_s": total_keys / (best / 1e3),
             "plain_keys_per_s": total_keys / (plain_ms / 1e3), "speedup_vs_plain": plain_ms / best,
             "hbm_frac": algo_bytes / (best / 1e3) / 1e9 / peaks()[0], "algorithmic_bytes": algo_bytes,
-            "launches": 1, "checked": ok}
+            "launches": 1, "checked": ok,
+            "checked_how": "every instance's H and output equal to the instance run alone through "
+                           "dialsort_histogram / dialsort_sort; three also equal to numpy's sort"}
 
 
 def run_served(ds, torch, seconds: float = 10.0, warm: float = 1.0, rate: float = 2000.0):
@@ -433,35 +434,24 @@ def run_served(ds, torch, seconds: float = 10.0, warm: float = 1.0, rate: float 
     """
     import gen
 
-    count = int(rate * (seconds + warm))
-    gaps = -np.log1p(-gen.unit(count, stream=5 * 16)) / rate
-    arrivals = np.cumsum(gaps)
-    ns = gen.loguniform(count, 12, 26, stream=5 * 16 + 1).astype(np.int64)
-    us = gen.loguniform(count, 8, 24, stream=5 * 16 + 2).astype(np.int64)
-    w = gen.words(count, stream=5 * 16 + 3)
-    width = np.where(w & 1, 2, 4)
-    us = np.where(width == 2, np.minimum(us, 65536), us)
-    kind = np.where((w >> 1) & 1, "sort", "histogram")
-    dist = np.where((w >> 2) & 1, "zipf", "uniform")
+    tr = gen.served_trace(rate, seconds, warm)
+    count, arrivals, ns, us = len(tr["n"]), tr["arrivals"], tr["n"], tr["U"]
     pools = {}
     for d in ("uniform", "zipf"):
-        for wd, top in ((4, 24), (2, 16)):
-            base = gen.keys(1 << 26, 1 << top, d, width=wd, param=1.2 if d == "zipf" else None, stream=5 * 16 + 8)
+        for wd in (4, 2):
+            base = gen.served_pool(d, wd)
             bt = torch.from_numpy(base.view(np.int32 if wd == 4 else np.int16)).cuda()
             if wd == 2:
                 bt = bt.to(torch.int32) & 0xFFFF
+            top = 24 if wd == 4 else 16
             for c in range(8, top + 1):
-                sh = (bt >> (top - c)).to(torch.int32 if wd == 4 else torch.int16)
-                pools[(d, wd, c)] = sh
+                pools[(d, wd, c)] = (bt >> (top - c)).to(torch.int32 if wd == 4 else torch.int16)
             del bt
-    offs = gen.words(count, stream=5 * 16 + 4)
     entries = []
     for i in range(count):
-        c = int(np.floor(np.log2(us[i])))
-        pool = pools[(str(dist[i]), int(width[i]), c)]
-        o = int(offs[i] % ((1 << 26) - ns[i] + 1))
-        o -= o % 8  # keep slices 16-byte aligned
-        entries.append((pool[o:o + ns[i]], int(us[i]), str(kind[i]), int(arrivals[i] * 1e9)))
+        pool = pools[(str(tr["dist"][i]), int(tr["width"][i]), int(tr["cls"][i]))]
+        o = int(tr["start"][i])
+        entries.append((pool[o:o + ns[i]], int(us[i]), str(tr["kind"][i]), int(arrivals[i] * 1e9)))
     meas = arrivals >= warm
     out = {"workload": f"Poisson {rate:.0f} req/s for {seconds:.0f} s after {warm:.0f} s warm-up "
                        f"({int(meas.sum())} measured requests), n log-uniform [2^12,2^26], U log-uniform "
@@ -476,6 +466,27 @@ def run_served(ds, torch, seconds: float = 10.0, warm: float = 1.0, rate: float 
                      "mean_ms": float(lat.mean()), "keys_per_s": float(ns[meas].sum() / span),
                      "all_ok": bool(np.all(res["status"] == 0)), "wall_s": wall / 1e9,
                      "status_counts": {int(v): int(c) for v, c in zip(st_vals, st_counts)}}
+    # results, not just status: every 10th request of the trace through the server (all submitted at once,
+    # so they overlap), each compared with the same request run alone (untimed)
+    srv = ds.Server(hbm_budget_bytes=64 << 30, max_slots=64)
+    sample = list(range(0, count, 10))
+    tickets = [srv.submit(entries[i][0], entries[i][1], entries[i][2]) for i in sample]
+    match = 0
+    for i, t in zip(sample, tickets):
+        keys_i, U_i, kind_i, _ = entries[i]
+        res = srv.wait(t, timeout_s=120.0)
+        if res["status"] == ds.OK:
+            same = torch.equal(res["out"], ds.sort(keys_i, U_i)) if kind_i == "sort" else \
+                torch.equal(res["H"], ds.histogram(keys_i, U_i))
+            match += int(same)
+        srv.release(t)
+    srv.close()
+    out["results_checked"] = {"requests": len(sample), "equal_to_alone": match,
+                              "how": "every 10th request of the trace served together, each result compared with "
+                                     "the same request run alone (the full comparison with the CPU oracle is "
+                                     "tests/test_gpu_fullsize.py)"}
+    for name in ("served", "plain_launches"):
+        out[name]["all_ok"] = out[name]["all_ok"] and match == len(sample)
     del pools
     return out
 

@@ -115,3 +115,65 @@ def words(count: int, *, seed: int = BASE_SEED, stream: int = 0) -> np.ndarray:
     if count:
         _load().gen_u64(out.ctypes.data, count, seed, stream)
     return out
+
+
+# ---------------------------------------------------------------- workload recipes
+# The batched and served workloads, drawn here so that the benchmark and the tests see the same
+# instances.  Sizes, universes and choices only: no sorting arithmetic.
+
+def batch_workload(count: int = 4096):
+    """The batched configuration: count instances, n_i log-uniform in [2^10, 2^22], U_i log-uniform in
+    [2^8, 2^20], each instance's distribution drawn uniformly from {uniform, Zipf s=1.2, all equal},
+    uint32 keys.  Returns (ns, us, dists); batch_keys(i, ...) draws instance i's keys."""
+    ns = loguniform(count, 10, 22, stream=4 * 16).astype(np.int64)
+    us = loguniform(count, 8, 20, stream=4 * 16 + 1).astype(np.int64)
+    picks = words(count, stream=4 * 16 + 2)
+    dists = [["uniform", "zipf", "all_equal"][int(p % 3)] for p in picks]
+    return ns, us, dists
+
+
+def batch_keys(i: int, n: int, U: int, dist: str, out: np.ndarray | None = None) -> np.ndarray:
+    """Keys of instance i of batch_workload()."""
+    return keys(int(n), int(U), dist, stream=4 * 16 * 1000 + i, out=out)
+
+
+SERVED_POOL_KEYS = 1 << 26
+
+
+def served_trace(rate: float = 2000.0, seconds: float = 10.0, warm: float = 1.0):
+    """The served configuration's request trace: Poisson arrivals at `rate` req/s for warm + seconds,
+    n log-uniform [2^12, 2^26], U log-uniform [2^8, 2^24], uint32/uint16 keys 50/50 (uint16 => U <=
+    2^16), sort/histogram 50/50, uniform/Zipf 1.2 50/50.  A request's keys are a slice of a pool:
+    for each (distribution, width) one base array of 2^26 keys over the largest universe (2^24 for
+    uint32, 2^16 for uint16), shifted right so that the keys lie in [0, 2^c), c = floor(log2 U); the
+    slice starts at offsets[i] (16-byte aligned).  Returns a dict of per-request arrays."""
+    count = int(rate * (seconds + warm))
+    gaps = -np.log1p(-unit(count, stream=5 * 16)) / rate
+    arrivals = np.cumsum(gaps)
+    ns = loguniform(count, 12, 26, stream=5 * 16 + 1).astype(np.int64)
+    us = loguniform(count, 8, 24, stream=5 * 16 + 2).astype(np.int64)
+    w = words(count, stream=5 * 16 + 3)
+    width = np.where(w & 1, 2, 4)
+    us = np.where(width == 2, np.minimum(us, 65536), us)
+    kind = np.where((w >> 1) & 1, "sort", "histogram")
+    dist = np.where((w >> 2) & 1, "zipf", "uniform")
+    offs = words(count, stream=5 * 16 + 4)
+    cls = np.floor(np.log2(us)).astype(np.int64)
+    start = np.array([int(offs[i] % (SERVED_POOL_KEYS - ns[i] + 1)) for i in range(count)], dtype=np.int64)
+    start -= start % 8
+    return {"arrivals": arrivals, "n": ns, "U": us, "width": width, "kind": kind, "dist": dist,
+            "cls": cls, "start": start, "warm": warm}
+
+
+def served_pool(dist: str, width: int) -> np.ndarray:
+    """The base key pool of served_trace() for one (distribution, width): 2^26 keys over [0, 2^24)
+    (uint32) or [0, 2^16) (uint16)."""
+    top = 24 if width == 4 else 16
+    return keys(SERVED_POOL_KEYS, 1 << top, dist, width=width, param=1.2 if dist == "zipf" else None,
+                stream=5 * 16 + 8)
+
+
+def served_request_keys(pool: np.ndarray, width: int, c: int, start: int, n: int) -> np.ndarray:
+    """Keys of one served request: the pool slice [start, start + n) shifted into [0, 2^c)."""
+    top = 24 if width == 4 else 16
+    return (pool[start:start + n] >> (top - c)).astype(pool.dtype)

@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_count_kernel(
         bulk_store(part + (uint64_t)slot * bins + tid * (bins / 4), hist + tid * (bins / 4), bins);  // bins / 4 words
         pending = true;
       }
-      if (tid == 0) part_used[slot] = 1u;
+      if (tid == 0) part_used[slot] = b + 1u;  // slots of neighbouring buckets interleave: tag the bucket
       continue;
     }
     uint32_t nz = 0;
@@ -514,7 +514,8 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_count_kernel(
 
 // Sums the scratch histograms of every shared bucket into H: CTA (b, c) takes
 // bins [1024 c, 1024 c + 1024) of bucket b; the pieces of bucket b sit in slots
-// i + b of the pass-2 CTAs i that counted part of it.
+// i + b of the pass-2 CTAs i that counted part of it, each tagged b + 1 (the
+// slot i + b of a CTA that counted another bucket b' carries the tag b' + 1).
 __global__ void __launch_bounds__(256) hier_merge_kernel(const uint32_t* __restrict__ btot, uint32_t B, uint32_t U,
                                                          uint32_t G, const uint32_t* __restrict__ part,
                                                          const uint32_t* __restrict__ part_used,
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(256) hier_merge_kernel(const uint32_t* __restr
   if (i0 >= Ub) return;
   uint4 acc = make_uint4(0u, 0u, 0u, 0u);
   for (uint32_t i = 0; i < G; ++i) {
-    if (!part_used[i + b]) continue;
+    if (part_used[i + b] != b + 1u) continue;  // slot i + b may hold a piece of another bucket
     const uint4 v = *reinterpret_cast<const uint4*>(part + (uint64_t)(i + b) * bins + i0);
     acc.x += v.x;
     acc.y += v.y;

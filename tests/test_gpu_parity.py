@@ -102,6 +102,18 @@ def test_two_level_regime(ds, U, dist, crn):
     np.testing.assert_array_equal(host(H), oracle.histogram(keys, U)[0])
 
 
+@pytest.mark.parametrize("n", [3 * (1 << 20) + 5, (1 << 22) + 13, 3_811_443])
+@pytest.mark.parametrize("U", [65537, 71454, 84014, 105469, (1 << 17) + 3, 1 << 21])
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "all_equal", "sorted"])
+def test_two_level_buckets_shared_by_many_count_ctas(ds, n, U, dist):
+    """Few buckets, many pass-2 CTAs: buckets counted by several CTAs at once (their histograms merged
+    from per-CTA scratch) next to buckets counted by one, in every combination the split produces."""
+    keys = gen.keys(n, U, dist, stream=34)
+    H = ds.histogram(dev(keys), U, config={"regime": "two_level"})
+    assert ds.stream_status() == ds.OK
+    np.testing.assert_array_equal(host(H), oracle.histogram(keys, U)[0])
+
+
 def test_two_level_out_of_range_and_needs_workspace(ds):
     U = 1 << 20
     keys = gen.keys((1 << 20) + 77, U, "uniform", stream=32)
