@@ -2,7 +2,9 @@
 // host-side argument checks, per-device state, and the launch sequences of the
 // two steps of DialSort.
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 #include "internal.h"
@@ -37,6 +39,8 @@ const DeviceInfo* device_info() {
     d.smem_optin = (size_t)v;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) return;
     d.pageable = v != 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return;
+    d.cooperative = v != 0;
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return;
     d.err = static_cast<uint32_t*>(p);
@@ -44,6 +48,43 @@ const DeviceInfo* device_info() {
     g_dev[dev] = d;
   });
   return g_dev[dev].device == dev ? &g_dev[dev] : nullptr;
+}
+
+namespace {
+std::mutex g_cfg_mu;
+std::map<std::tuple<int, const void*, int>, bool> g_cfg_done;                    // (device, kernel, carve-out)
+std::map<std::tuple<int, const void*, int, size_t>, int> g_cfg_occupancy;       // (device, kernel, threads, smem)
+}  // namespace
+
+cudaError_t kernel_config(const void* fn, int threads, size_t dyn_smem, bool carveout_max, int* per_sm) {
+  const DeviceInfo* dev = device_info();
+  if (!dev) return cudaErrorNoDevice;
+  std::lock_guard<std::mutex> lock(g_cfg_mu);
+  const auto key = std::make_tuple(dev->device, fn, carveout_max ? 1 : 0);
+  if (!g_cfg_done.count(key)) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    // the opt-in limit covers static and dynamic shared memory together
+    const size_t room = dev->smem_optin > fa.sharedSizeBytes ? dev->smem_optin - fa.sharedSizeBytes : 0;
+    if (room > 48u * 1024u) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room);
+    if (e == cudaSuccess && carveout_max)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    g_cfg_done[key] = true;
+  }
+  if (per_sm) {
+    const auto okey = std::make_tuple(dev->device, fn, threads, dyn_smem);
+    auto it = g_cfg_occupancy.find(okey);
+    if (it == g_cfg_occupancy.end()) {
+      int v = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn, threads, dyn_smem);
+      if (e != cudaSuccess) return e;
+      it = g_cfg_occupancy.emplace(okey, v).first;
+    }
+    *per_sm = it->second;
+  }
+  return cudaSuccess;
 }
 
 dialsort_status_t kernel_address(const void* p, const DeviceInfo& dev, const void** q, bool* in_host) {
@@ -151,9 +192,7 @@ dialsort_status_t reconstruct_impl(const uint32_t* H, uint32_t U, void* out, uin
   if (s != DIALSORT_OK) return s;
   H = static_cast<const uint32_t*>(hp);
   if (n) out = const_cast<void*>(op);
-  cudaError_t e = launch_offsets(H, U, n, ws, L, dev->err, st);
-  if (e == cudaSuccess) e = launch_expand(H, U, n, out, out_bytes, ws, L, st);
-  return from_cuda(e);
+  return from_cuda(launch_projection(H, U, n, out, out_bytes, ws, L, *dev, dev->err, st));
 }
 
 size_t sort_h_bytes(uint32_t U) { return align_up((size_t)U * 4, 256); }
@@ -168,6 +207,18 @@ dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, ui
   if (ws == nullptr || !aligned(ws, 256) || ws_bytes < hb + rb + ib) return DIALSORT_ERR_WORKSPACE;
   char* base = static_cast<char*>(ws);
   uint32_t* H = reinterpret_cast<uint32_t*>(base);
+  if (small_sort_fits(n, U, key_bytes)) {
+    // a small input: the whole sort in one launch
+    const DeviceInfo* dev = device_info();
+    if (!dev) return DIALSORT_ERR_CUDA;
+    if (dev->cooperative) {
+      const void *kp, *op;
+      if ((s = kernel_address(keys, *dev, &kp)) != DIALSORT_OK) return s;
+      if ((s = kernel_address(out, *dev, &op)) != DIALSORT_OK) return s;
+      return from_cuda(launch_small_sort(kp, key_bytes, n, U, H, const_cast<void*>(op), base + hb, recon_layout(U, n),
+                                         *dev, dev->err, st));
+    }
+  }
   s = histogram_impl(keys, key_bytes, n, U, H, nullptr, ib ? base + hb + rb : nullptr, ib, st);
   if (s != DIALSORT_OK) return s;
   return reconstruct_impl(H, U, out, key_bytes, n, base + hb, rb, st);
@@ -205,8 +256,8 @@ dialsort_status_t sort_mapped_impl(const void* keys, uint32_t key_bytes, uint64_
   cudaError_t e = cudaMemsetAsync(H, 0, (size_t)U * 4, st);
   if (e == cudaSuccess && n > 0)
     e = launch_histogram(kp, key_bytes, n, U, H, plan, dev->err, st, static_cast<const uint32_t*>(pp), M);
-  if (e == cudaSuccess) e = launch_offsets(H, U, n, base + hb, L, dev->err, st);
-  if (e == cudaSuccess) e = launch_expand(H, U, n, const_cast<void*>(op), key_bytes, base + hb, L, st, ip);
+  if (e == cudaSuccess)
+    e = launch_projection(H, U, n, const_cast<void*>(op), key_bytes, base + hb, L, *dev, dev->err, st, ip);
   return from_cuda(e);
 }
 
@@ -309,7 +360,7 @@ dialsort_status_t dialsort_offsets(const uint32_t* H, uint32_t U, uint64_t n, vo
   if (ws == nullptr || !aligned(ws, 256) || ws_bytes < L.total) return DIALSORT_ERR_WORKSPACE;
   const DeviceInfo* dev = device_info();
   if (!dev) return DIALSORT_ERR_CUDA;
-  return from_cuda(launch_offsets(H, U, n, ws, L, dev->err, as_stream(stream)));
+  return from_cuda(launch_projection(H, U, n, nullptr, 4, ws, L, *dev, dev->err, as_stream(stream), nullptr, 1));
 }
 
 dialsort_status_t dialsort_read_chunk_offsets(const void* ws, uint32_t U, uint64_t n, uint64_t* chunk_offsets,

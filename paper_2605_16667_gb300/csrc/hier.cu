@@ -606,7 +606,7 @@ cudaError_t launch_hier(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* 
                               : (pow2 ? reinterpret_cast<const void*>(&hier_partition_kernel<64, true>)
                                       : reinterpret_cast<const void*>(&hier_partition_kernel<64, false>));
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p1, kP1Threads, 0);
+  e = kernel_config(p1, kP1Threads, 0, false, &per_sm);
   if (e != cudaSuccess) return e;
   const uint64_t grid1 = std::min<uint64_t>(T.num_tiles, (uint64_t)dev.sms * std::max(per_sm, 1));
   {
@@ -621,7 +621,7 @@ cudaError_t launch_hier(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* 
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (!accumulate && (e = cudaMemsetAsync(H, 0, (size_t)U * 4, stream)) != cudaSuccess) return e;
   const size_t p2_smem = (size_t)4 << kLow;
-  e = cudaFuncSetAttribute(hier_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_smem);
+  e = kernel_config(reinterpret_cast<const void*>(&hier_count_kernel), kP2Threads, p2_smem, false, nullptr);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(part_used, 0, 4 * ((size_t)G + T.B), stream)) != cudaSuccess) return e;
   hier_count_kernel<<<G, kP2Threads, p2_smem, stream>>>(low, seg, start, btot, T.B, U, T.num_tiles, T.S_t, H, part,

@@ -92,7 +92,7 @@ cudaError_t launch_histogram(const void* keys, uint32_t key_bytes, uint64_t n, u
                              uint32_t M) {
   const void* fn = pick_kernel(key_bytes, mode_of(plan.regime));
   if (plan.smem_bytes > 48u * 1024u) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes);
+    cudaError_t e = kernel_config(fn, (int)plan.threads, plan.smem_bytes, false, nullptr);
     if (e != cudaSuccess) return e;
   }
   uint32_t replicas = plan.replicas, wpc = plan.words_per_copy, crn = plan.crn;

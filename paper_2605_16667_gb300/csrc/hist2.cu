@@ -655,10 +655,8 @@ cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   cudaError_t e = cudaMemsetAsync(btot, 0, 4 * (size_t)T.B, stream);
   if (e != cudaSuccess) return e;
   const size_t p1_smem = 4 * (size_t)p1_words(T.B);
-  e = cudaFuncSetAttribute(partition_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem);
-  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, partition_kernel, kP1Threads, p1_smem);
+  e = kernel_config(reinterpret_cast<const void*>(&partition_kernel), kP1Threads, p1_smem, false, &per_sm);
   if (e != cudaSuccess) return e;
   const uint64_t grid1 = std::min<uint64_t>(T.num_tiles, (uint64_t)dev.sms * std::max(per_sm, 1));
   partition_kernel<<<(unsigned)grid1, kP1Threads, p1_smem, stream>>>(keys, n, U, T.L, T.B, T.num_tiles, low, toff,
@@ -676,7 +674,7 @@ cudaError_t launch_two_level(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   const void* fn = T.p2_smem32 ? reinterpret_cast<const void*>(&bucket_kernel<MODE_SMEM32>)
                                : reinterpret_cast<const void*>(&bucket_kernel<MODE_SMEM16>);
   if (p2_smem > 48u * 1024u) {
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_smem);
+    e = kernel_config(fn, (int)p2_threads, p2_smem, false, nullptr);
     if (e != cudaSuccess) return e;
   }
   const uint16_t* lowc = low;

@@ -14,6 +14,7 @@ struct DeviceInfo {
   size_t smem_optin = 0;  // max dynamic shared memory per CTA (opt-in)
   uint32_t* err = nullptr;  // device address of the per-device error word
   bool pageable = false;    // kernels may dereference pageable host memory (coherent host page tables)
+  bool cooperative = false; // cooperative (all CTAs resident) launches are supported
 };
 
 // The address a kernel dereferences for a caller's pointer: device or managed
@@ -25,6 +26,12 @@ dialsort_status_t kernel_address(const void* p, const DeviceInfo& dev, const voi
 // Per-device properties and error word; initialised once per device, with
 // that device current.  Returns nullptr when no device is usable.
 const DeviceInfo* device_info();
+
+// Launch set-up of a kernel on the current device, done once per (device, kernel): its dynamic
+// shared-memory limit raised to the device's opt-in maximum and, with carveout_max, the shared-memory
+// carve-out preferred; *per_sm (optional) receives its resident CTAs per SM for the given block size and
+// dynamic shared memory, also computed once per configuration.
+cudaError_t kernel_config(const void* fn, int threads, size_t dyn_smem, bool carveout_max, int* per_sm);
 
 // Fully resolved launch choices for step 1.
 struct HistPlan {
@@ -104,6 +111,19 @@ ReconLayout recon_layout(uint32_t U, uint64_t n);
 
 cudaError_t launch_offsets(const uint32_t* H, uint32_t U, uint64_t n, void* ws, const ReconLayout& L,
                            uint32_t* err, cudaStream_t stream);
+// The projection with its offsets: one cooperative launch (offset scan, grid barrier, expansion of
+// the output tiles) where the device supports cooperative launches, else the offset scan then the
+// expansion kernel.  phase_mask 1: the offsets only (O[] and the tile table written); 3: both.
+bool projection_fused_fits(uint32_t U, uint64_t n);
+cudaError_t launch_projection(const uint32_t* H, uint32_t U, uint64_t n, void* out, uint32_t out_bytes, void* ws,
+                              const ReconLayout& L, const DeviceInfo& dev, uint32_t* err, cudaStream_t stream,
+                              const void* inv = nullptr, int phase_mask = 3);
+// A whole sort of a small input (n <= 2^22, U <= 4096) in one cooperative launch (zero H, count,
+// offsets, expand; rws is the reconstruction scratch).  small.cu
+bool small_sort_fits(uint64_t n, uint32_t U, uint32_t key_bytes);
+cudaError_t launch_small_sort(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H, void* out,
+                              void* rws, const ReconLayout& L, const DeviceInfo& dev, uint32_t* err,
+                              cudaStream_t stream);
 // inv (optional): index k is written as inv[k] (an array of out_bytes-wide values); out_bytes 1, 2 or 4.
 cudaError_t launch_expand(const uint32_t* H, uint32_t U, uint64_t n, void* out, uint32_t out_bytes, void* ws,
                           const ReconLayout& L, cudaStream_t stream, const void* inv = nullptr);
