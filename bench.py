@@ -466,6 +466,23 @@ def run_served(ds, torch, seconds: float = 10.0, warm: float = 1.0, rate: float 
                      "mean_ms": float(lat.mean()), "keys_per_s": float(ns[meas].sum() / span),
                      "all_ok": bool(np.all(res["status"] == 0)), "wall_s": wall / 1e9,
                      "status_counts": {int(v): int(c) for v, c in zip(st_vals, st_counts)}}
+    # rate sweep: the trace's first 4000 requests with their arrival gaps scaled to 2k, 8k and 32k req/s, and
+    # all at once (closed loop: the largest backlog), through the server and through plain launches
+    sweep_n = min(4000, count)
+    base_ns = np.array([e[3] for e in entries[:sweep_n]], dtype=np.float64)
+    sweep = []
+    for r in (2000.0, 8000.0, 32000.0, None):
+        scale = 0.0 if r is None else rate / r
+        ents = [(e[0], e[1], e[2], int(base_ns[i] * scale)) for i, e in enumerate(entries[:sweep_n])]
+        row = {"rate_req_s": r if r is not None else "closed loop (all at t = 0)", "requests": sweep_n}
+        for name, use_server in (("served", True), ("plain_launches", False)):
+            res, wall = ds.replay(ents, use_server=use_server, hbm_budget_bytes=64 << 30, max_slots=64)
+            lat = (res["done_ns"].astype(np.float64) - res["arrival_ns"].astype(np.float64)) / 1e6
+            span = (res["done_ns"].max() - res["arrival_ns"].min()) / 1e9
+            row[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "keys_per_s": float(ns[:sweep_n].sum() / span), "all_ok": bool(np.all(res["status"] == 0))}
+        sweep.append(row)
+    out["rate_sweep"] = sweep
     # results, not just status: every 10th request of the trace through the server (all submitted at once,
     # so they overlap), each compared with the same request run alone (untimed)
     srv = ds.Server(hbm_budget_bytes=64 << 30, max_slots=64)

@@ -39,8 +39,6 @@ const DeviceInfo* device_info() {
     d.smem_optin = (size_t)v;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) return;
     d.pageable = v != 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return;
-    d.cooperative = v != 0;
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return;
     d.err = static_cast<uint32_t*>(p);
@@ -211,13 +209,11 @@ dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, ui
     // a small input: the whole sort in one launch
     const DeviceInfo* dev = device_info();
     if (!dev) return DIALSORT_ERR_CUDA;
-    if (dev->cooperative) {
-      const void *kp, *op;
-      if ((s = kernel_address(keys, *dev, &kp)) != DIALSORT_OK) return s;
-      if ((s = kernel_address(out, *dev, &op)) != DIALSORT_OK) return s;
-      return from_cuda(launch_small_sort(kp, key_bytes, n, U, H, const_cast<void*>(op), base + hb, recon_layout(U, n),
-                                         *dev, dev->err, st));
-    }
+    const void *kp, *op;
+    if ((s = kernel_address(keys, *dev, &kp)) != DIALSORT_OK) return s;
+    if ((s = kernel_address(out, *dev, &op)) != DIALSORT_OK) return s;
+    return from_cuda(launch_small_sort(kp, key_bytes, n, U, H, const_cast<void*>(op), base + hb, recon_layout(U, n),
+                                       *dev, dev->err, st));
   }
   s = histogram_impl(keys, key_bytes, n, U, H, nullptr, ib ? base + hb + rb : nullptr, ib, st);
   if (s != DIALSORT_OK) return s;

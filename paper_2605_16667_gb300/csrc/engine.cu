@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   uint64_t idle_since = 0;  // thread 0 only
   uint32_t backoff = 500;   // ns; doubles while idle (every thread keeps the same value)
+  unsigned long long seen_bell = 0;  // thread 0 only: the doorbell value at the last ring scan
 
   for (;;) {
     // ---- find the oldest request with an unclaimed item, claim one.  The
@@ -221,28 +222,50 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
     }
     const uint32_t cmd = s_cmd;  // thread 0 writes it again only after the next loop-top barrier
 
-    // ---- nothing to do: wait (bounded), or leave
+    // ---- nothing to do: wait (bounded), or leave.  Served mode: in the first kQuickCtas CTAs thread 0
+    // watches the doorbell word (one load per poll, every 200 ns) and the ring is scanned again as soon
+    // as it rings, or after 64 quiet polls; the other CTAs, and batched mode, sleep with back-off.
     if (cmd == CMD_SLEEP) {
       if (tid == 0) {
-        const uint64_t now = globaltimer();
-        if (idle_since == 0) idle_since = now;
-        const uint64_t last = *(volatile unsigned long long*)&L.ctl->last_work;
         s_exit = 0;
-        if (L.served && L.host->stop) {
-          s_exit = 1;
-        } else if (now - idle_since > L.idle_ns && (now > last ? now - last : 0) > L.idle_ns) {
-          // the whole engine, not just this CTA, has had no work for idle_ns
-          if (!L.served) raise_error(L.err, ERRBIT_TIMEOUT);
-          s_exit = 1;
+        for (uint32_t polls = 0;; ++polls) {
+          const uint64_t now = globaltimer();
+          if (idle_since == 0) idle_since = now;
+          const uint64_t last = *(volatile unsigned long long*)&L.ctl->last_work;
+          if (L.served && L.host->stop) {
+            s_exit = 1;
+            break;
+          }
+          if (now - idle_since > L.idle_ns && (now > last ? now - last : 0) > L.idle_ns) {
+            // the whole engine, not just this CTA, has had no work for idle_ns
+            if (!L.served) raise_error(L.err, ERRBIT_TIMEOUT);
+            s_exit = 1;
+            break;
+          }
+          // batched mode, and served-mode CTAs outside the quick pool: back-off (they join a long
+          // request within its first phases; a short one is done by the pool)
+          if (!L.served || blockIdx.x >= kQuickCtas) {
+            __nanosleep(backoff);
+            break;
+          }
+          const unsigned long long b = *(volatile unsigned long long*)&L.ctl->bell;
+          if (b != seen_bell) {
+            seen_bell = b;
+            break;
+          }
+          if (polls >= 64) break;
+          __nanosleep(200);
         }
       }
       __syncthreads();
       if (s_exit) break;
-      __nanosleep(backoff);
       backoff = min(backoff * 2u, 16000u);
       continue;
     }
-    if (cmd == CMD_RETRY) continue;
+    if (cmd == CMD_RETRY) {  // another CTA took the item: let the claimers spread out
+      __nanosleep(100 + 32 * (blockIdx.x & 7u));
+      continue;
+    }
     backoff = 500;
     if (tid == 0) idle_since = 0;
 

@@ -12,6 +12,7 @@ namespace eng {
 constexpr uint32_t kThreads = 256;       // worker CTA size (the step-2 routines assume 256)
 constexpr uint32_t kZeroWords = 16384;   // H words zeroed per zero item (64 KB)
 constexpr uint32_t kWindow = 256;        // requests examined per work search (one per thread)
+constexpr uint32_t kQuickCtas = 32;      // served mode: CTAs that watch the doorbell (fast pick-up)
 constexpr uint32_t kHistSmem = 48 * 1024;  // dynamic shared memory for shared-memory histogram items
 
 enum Phase : uint32_t { PH_FREE = 0, PH_ZERO = 1, PH_HIST = 2, PH_OFFS = 3, PH_EXPAND = 4, PH_DONE = 5 };
@@ -86,7 +87,8 @@ struct Ctl {
   uint32_t tail;                 // batched mode: every request below tail is finished
   uint32_t pad0;
   unsigned long long last_work;  // %globaltimer of the latest claimed item (any CTA)
-  uint32_t pad[60];
+  unsigned long long bell;       // served mode: admissions so far, written by DMA after each slot is published
+  uint32_t pad[58];
 };
 
 struct Launch {

@@ -14,7 +14,6 @@ struct DeviceInfo {
   size_t smem_optin = 0;  // max dynamic shared memory per CTA (opt-in)
   uint32_t* err = nullptr;  // device address of the per-device error word
   bool pageable = false;    // kernels may dereference pageable host memory (coherent host page tables)
-  bool cooperative = false; // cooperative (all CTAs resident) launches are supported
 };
 
 // The address a kernel dereferences for a caller's pointer: device or managed
@@ -111,15 +110,13 @@ ReconLayout recon_layout(uint32_t U, uint64_t n);
 
 cudaError_t launch_offsets(const uint32_t* H, uint32_t U, uint64_t n, void* ws, const ReconLayout& L,
                            uint32_t* err, cudaStream_t stream);
-// The projection with its offsets: one cooperative launch (offset scan, grid barrier, expansion of
-// the output tiles) where the device supports cooperative launches, else the offset scan then the
-// expansion kernel.  phase_mask 1: the offsets only (O[] and the tile table written); 3: both.
-bool projection_fused_fits(uint32_t U, uint64_t n);
+// The projection with its offsets in one launch (offset-scan groups, then output tiles, in one ticket
+// order).  phase_mask 1: the offsets only (O[] and the tile table written); 3: both.
 cudaError_t launch_projection(const uint32_t* H, uint32_t U, uint64_t n, void* out, uint32_t out_bytes, void* ws,
                               const ReconLayout& L, const DeviceInfo& dev, uint32_t* err, cudaStream_t stream,
                               const void* inv = nullptr, int phase_mask = 3);
-// A whole sort of a small input (n <= 2^22, U <= 4096) in one cooperative launch (zero H, count,
-// offsets, expand; rws is the reconstruction scratch).  small.cu
+// A whole sort of a small input (n <= 2^22, U <= 4096) in one launch (zero H, count, offsets, expand;
+// rws is the reconstruction scratch).  small.cu
 bool small_sort_fits(uint64_t n, uint32_t U, uint32_t key_bytes);
 cudaError_t launch_small_sort(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint32_t* H, void* out,
                               void* rws, const ReconLayout& L, const DeviceInfo& dev, uint32_t* err,

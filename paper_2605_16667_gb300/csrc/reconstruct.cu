@@ -56,68 +56,69 @@ __global__ void __launch_bounds__(kReconThreads, 6) expand_kernel(const uint32_t
 
 
 // ---------------------------------------------------------------- fused projection
-// The offsets and the expansion in one cooperative launch:
-//   phase 1  the offset scan: CTAs take groups of eight 1024-bin chunks in
-//            ticket order, sum them and chain the groups by decoupled look-back
-//            (O[c] = first output position of chunk c, and each output tile's
-//            first chunk), as offsets_kernel does;
-//   barrier  a grid-wide barrier (every CTA is resident: cooperative launch;
-//            the wait is bounded and records ERRBIT_TIMEOUT if it runs out);
-//   phase 2  the CTAs claim the 8192-key output tiles one at a time from a
-//            second ticket (expand_tile).
-// With phase_mask = 1 only phase 1 runs: the offsets step timed on its own.
+// The offsets and the expansion in one launch.  Work items are handed out in
+// one ticket order: first the groups of eight 1024-bin chunks of the offset
+// scan (chunk sums chained by decoupled look-back: O[c], and each output
+// tile's first chunk), then the 8192-key output tiles.  A CTA holding a tile
+// first waits (bounded) until every group is done; every group has a lower
+// ticket, so it is held by a running CTA or finished, and the wait ends
+// without any assumption about how many CTAs are resident.
+// With phase_mask = 1 only the groups are handed out: the offsets step timed
+// on its own.
 struct ProjSmem {
   __align__(16) ExpandSmem ex;  // first, 16-byte aligned: its tile buffer is read and written as uint4
   OffsetsSmem off;
-  uint32_t g;  // phase-1 ticket
+  uint32_t k;  // ticket
 };
 static_assert(offsetof(ProjSmem, ex) % 16 == 0, "the expansion buffer must be 16-byte aligned");
 
+// Counters of one projection (in the zeroed part of the workspace).
+struct ProjCtl {
+  uint32_t ticket;       // next work item
+  uint32_t groups_done;  // finished groups of the offset scan
+};
+
 template <typename OutT>
 __global__ void __launch_bounds__(kReconThreads) project_kernel(const uint32_t* __restrict__ H, uint32_t U,
-                                                                uint64_t n_cap, uint64_t num_chunks, uint32_t* ticket,
-                                                                uint32_t* arrived, uint64_t* desc, uint64_t* O,
-                                                                uint32_t* first_chunk, OutT* __restrict__ out,
-                                                                int out_aligned, const OutT* __restrict__ inv,
-                                                                uint32_t* err, int phase_mask) {
+                                                                uint64_t n_cap, uint64_t num_chunks, ProjCtl* ctl,
+                                                                uint64_t* desc, uint64_t* O, uint32_t* first_chunk,
+                                                                OutT* __restrict__ out, int out_aligned,
+                                                                const OutT* __restrict__ inv, uint32_t* err,
+                                                                int phase_mask) {
   __shared__ __align__(16) ProjSmem sm;
   const uint32_t tid = threadIdx.x;
   const uint64_t groups = offset_groups(num_chunks);
-  // ---- phase 1: offsets
+  const uint64_t tiles = (phase_mask & 2) ? (n_cap + kTileKeys - 1) / kTileKeys : 0;
+  bool waited = false;
   for (;;) {
-    if (tid == 0) sm.g = atomicAdd(ticket, 1u);
+    if (tid == 0) sm.k = atomicAdd(&ctl->ticket, 1u);
     __syncthreads();
-    const uint64_t g = sm.g;
+    const uint64_t k = sm.k;
     __syncthreads();
-    if (g >= groups) break;
-    offsets_group(H, U, n_cap, num_chunks, g, desc, O, first_chunk, err, sm.off);
-  }
-  // ---- grid barrier (bounded): every thread's O and table writes are fenced before the arrival
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    atomicAdd(arrived, 1u);
-    uint32_t spins = 0;
-    while (*reinterpret_cast<volatile uint32_t*>(arrived) < gridDim.x) {
-      if (++spins > kSpinLimit) {
-        raise_error(err, ERRBIT_TIMEOUT);
-        break;
-      }
-      __nanosleep(64);
+    if (k >= groups + tiles) break;
+    if (k < groups) {
+      offsets_group(H, U, n_cap, num_chunks, k, desc, O, first_chunk, err, sm.off);
+      __threadfence();  // every thread's O and table writes, before the group counts as done
+      __syncthreads();
+      if (tid == 0) atomicAdd(&ctl->groups_done, 1u);
+      continue;
     }
-    __threadfence();
-  }
-  __syncthreads();
-  if (!(phase_mask & 2)) return;
-  // ---- phase 2: the output tiles, claimed one at a time (tiles differ in cost: dense or sparse runs)
-  const uint64_t num_tiles = (n_cap + kTileKeys - 1) / kTileKeys;
-  for (;;) {
-    if (tid == 0) sm.g = atomicAdd(arrived + 1, 1u);
-    __syncthreads();
-    const uint64_t t = sm.g;
-    __syncthreads();
-    if (t >= num_tiles) break;
-    expand_tile<OutT>(H, U, n_cap, num_chunks, O, first_chunk, out, out_aligned, t, sm.ex, inv);
+    if (!waited) {  // the offsets are complete before any tile is expanded
+      if (tid == 0) {
+        uint32_t spins = 0;
+        while (*reinterpret_cast<volatile uint32_t*>(&ctl->groups_done) < groups) {
+          if (++spins > kSpinLimit) {
+            raise_error(err, ERRBIT_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      waited = true;
+    }
+    expand_tile<OutT>(H, U, n_cap, num_chunks, O, first_chunk, out, out_aligned, k - groups, sm.ex, inv);
   }
 }
 
@@ -203,18 +204,11 @@ cudaError_t launch_expand(const uint32_t* H, uint32_t U, uint64_t n, void* out, 
 
 namespace dialsort {
 
-bool projection_fused_fits(uint32_t U, uint64_t n) { return n > 0 && U > 0; }
-
 cudaError_t launch_projection(const uint32_t* H, uint32_t U, uint64_t n, void* out, uint32_t out_bytes, void* ws,
                               const ReconLayout& L, const DeviceInfo& dev, uint32_t* err, cudaStream_t stream,
                               const void* inv, int phase_mask) {
-  if (!projection_fused_fits(U, n) || !dev.cooperative) {
-    cudaError_t e = launch_offsets(H, U, n, ws, L, err, stream);
-    if (e != cudaSuccess || phase_mask == 1) return e;
-    return launch_expand(H, U, n, out, out_bytes, ws, L, stream, inv);
-  }
   char* base = static_cast<char*>(ws);
-  cudaError_t e = cudaMemsetAsync(base, 0, L.clear_bytes, stream);  // ticket, barrier count, descriptors
+  cudaError_t e = cudaMemsetAsync(base, 0, L.clear_bytes, stream);  // counters, descriptors
   if (e != cudaSuccess) return e;
   const void* fn = out_bytes == 4   ? reinterpret_cast<const void*>(&project_kernel<uint32_t>)
                    : out_bytes == 2 ? reinterpret_cast<const void*>(&project_kernel<uint16_t>)
@@ -223,20 +217,26 @@ cudaError_t launch_projection(const uint32_t* H, uint32_t U, uint64_t n, void* o
   int per_sm = 0;
   e = kernel_config(fn, kReconThreads, 0, true, &per_sm);
   if (e != cudaSuccess) return e;
-  const uint64_t work = std::max<uint64_t>(L.num_tiles, offset_groups(L.num_chunks));
+  const uint64_t work = offset_groups(L.num_chunks) + (phase_mask & 2 ? L.num_tiles : 0);
   const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)dev.sms * std::max(per_sm, 1), std::max<uint64_t>(work, 1));
-  uint32_t* ticket = reinterpret_cast<uint32_t*>(base + L.off_ticket);
-  uint32_t* arrived = ticket + 1;  // arrived[0]: barrier count, arrived[1]: tile ticket (in the cleared region)
+  ProjCtl* ctl = reinterpret_cast<ProjCtl*>(base + L.off_ticket);  // in the zeroed region
   uint64_t* desc = reinterpret_cast<uint64_t*>(base + L.off_desc);
   uint64_t* O = reinterpret_cast<uint64_t*>(base + L.off_offsets);
   uint32_t* first = reinterpret_cast<uint32_t*>(base + L.off_first);
-  uint64_t nc = L.num_chunks, ncap = n;
-  uint32_t UU = U;
-  int aligned = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
-  int pm = phase_mask;
-  void* args[] = {const_cast<uint32_t**>(&H), &UU, &ncap, &nc, &ticket, &arrived, &desc, &O, &first, &out,
-                  &aligned, const_cast<void**>(&inv), &err, &pm};
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kReconThreads), args, 0, stream);
+  const int aligned = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+  if (out_bytes == 4)
+    project_kernel<uint32_t><<<grid, kReconThreads, 0, stream>>>(H, U, n, L.num_chunks, ctl, desc, O, first,
+                                                                 static_cast<uint32_t*>(out), aligned,
+                                                                 static_cast<const uint32_t*>(inv), err, phase_mask);
+  else if (out_bytes == 2)
+    project_kernel<uint16_t><<<grid, kReconThreads, 0, stream>>>(H, U, n, L.num_chunks, ctl, desc, O, first,
+                                                                 static_cast<uint16_t*>(out), aligned,
+                                                                 static_cast<const uint16_t*>(inv), err, phase_mask);
+  else
+    project_kernel<uint8_t><<<grid, kReconThreads, 0, stream>>>(H, U, n, L.num_chunks, ctl, desc, O, first,
+                                                                static_cast<uint8_t*>(out), aligned,
+                                                                static_cast<const uint8_t*>(inv), err, phase_mask);
+  return cudaGetLastError();
 }
 
 }  // namespace dialsort

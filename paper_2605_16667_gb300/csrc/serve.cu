@@ -125,6 +125,8 @@ struct dialsort_server_s {
   Req* h_req_stage = nullptr;    // pinned, one per slot
   State* h_state_stage = nullptr;
   unsigned long long* h_word_stage = nullptr;
+  unsigned long long* h_bell_stage = nullptr;  // per slot: the doorbell value its admission wrote
+  unsigned long long bells = 0;
   Ctl* d_ctl_dev = nullptr;
   cudaStream_t engine_stream = nullptr, copy_stream = nullptr;
   cudaEvent_t engine_done = nullptr;
@@ -185,6 +187,11 @@ struct dialsort_server_s {
       e = cudaMemcpyAsync(&d_states[s], &st, sizeof(State), cudaMemcpyHostToDevice, copy_stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(&d_states[s].word, &h_word_stage[s], 8, cudaMemcpyHostToDevice, copy_stream);
+    // then the doorbell (from this slot's own staging word, which stays put until the slot is reused):
+    // idle engine CTAs watch this one word and scan the ring when it changes
+    h_bell_stage[s] = ++bells;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&d_ctl_dev->bell, &h_bell_stage[s], 8, cudaMemcpyHostToDevice, copy_stream);
     if (e != cudaSuccess) {
       arena.release(block);
       fatal = DIALSORT_ERR_CUDA;
@@ -297,6 +304,7 @@ void destroy_server(dialsort_server_s* s) {
   if (s->h_req_stage) cudaFreeHost(s->h_req_stage);
   if (s->h_state_stage) cudaFreeHost(s->h_state_stage);
   if (s->h_word_stage) cudaFreeHost(s->h_word_stage);
+  if (s->h_bell_stage) cudaFreeHost(s->h_bell_stage);
   if (s->d_ctl_dev) cudaFree(s->d_ctl_dev);
   delete s;
 }
@@ -347,6 +355,7 @@ dialsort_status_t dialsort_server_create(const dialsort_server_cfg_t* cfg, dials
             cudaMallocHost(&s->h_req_stage, sizeof(Req) * s->slots) == cudaSuccess &&
             cudaMallocHost(&s->h_state_stage, sizeof(State) * s->slots) == cudaSuccess &&
             cudaMallocHost(&s->h_word_stage, sizeof(unsigned long long) * s->slots) == cudaSuccess &&
+            cudaMallocHost(&s->h_bell_stage, sizeof(unsigned long long) * s->slots) == cudaSuccess &&
             cudaMalloc(&s->d_ctl_dev, sizeof(Ctl)) == cudaSuccess &&
             cudaStreamCreateWithFlags(&s->engine_stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
