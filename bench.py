@@ -50,8 +50,10 @@ def parse():
     p.add_argument("--served-seconds", type=float, default=10.0)
     p.add_argument("--reference-seconds", type=float, default=60.0,
                    help="host time the reference arm (the oracle) spends on its timed and warm-up steps")
-    p.add_argument("--form", default="all", choices=["all", "batched", "served", "radix", "paper"],
-                   help="print only one form's measurement (batched, served, radix, or the paper's workload grid)")
+    p.add_argument("--form", default="all",
+                   choices=["all", "batched", "served", "radix", "paper", "autotune", "chunked"],
+                   help="print only one form's measurement (batched, served, radix, the paper's workload grid, "
+                        "or the autotuner against the cost model)")
     # workload-size overrides, for profiling smaller cases of the same kernels
     p.add_argument("--n", type=int, default=N_KEYS)
     p.add_argument("--U", type=int, default=UNIVERSE)
@@ -341,6 +343,130 @@ def run_paper(ds, torch, stream, runs: int = 7, warm: int = 3):
             "status": ds.stream_status()}
 
 
+def run_autotune(ds, torch, stream, n: int = 1 << 27, reps: int = 7):
+    """The universe sweep (n = 2^27 keys; U in {2^8, 2^12, 2^16, 2^20, 2^24, 2^26}, uniform and Zipf s = 1.1,
+    plus 16-bit keys with U = 2^16): step 1 as the cost model plans it with no skew information (the
+    planner without a table) against the measured table's plan for the probed skew class."""
+    import os
+
+    from paper_2605_16667_gb300 import tune
+
+    if not os.path.exists(ds.TUNE_TABLE):
+        return {"unavailable": "no measured tuning table next to the library"}
+    cases = [(U, 4, d) for U in (1 << 8, 1 << 12, 1 << 16, 1 << 20, 1 << 24, 1 << 26) for d in ("uniform", "zipf")]
+    cases += [(1 << 16, 2, "uniform"), (1 << 16, 2, "zipf")]
+
+    def med(keys, U, skew):
+        H = torch.empty(U, dtype=torch.int32, device="cuda")
+        ws = torch.empty(max(ds.histogram_workspace_size(n, U, keys.element_size()), 256), dtype=torch.uint8,
+                         device="cuda")
+        for _ in range(2):
+            ds.histogram(keys, U, H, ws=ws, skew=skew, stream=stream)
+        t = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ds.histogram(keys, U, H, ws=ws, skew=skew, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            t.append(a.elapsed_time(b))
+        t.sort()
+        return t[len(t) // 2], H
+
+    rows = []
+    for U, w, d in cases:
+        keys = tune.keys_for(n, U, w, 2 if d == "zipf" else 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        probe = ds.probe_skew(keys, U, stream)
+        probe_ms = (time.perf_counter() - t0) * 1e3
+        ds.tune_table_load(None)
+        model_plan = ds.plan_histogram(n, U, w, 0)
+        t_model, H_model = med(keys, U, None)
+        ds.tune_table_load(ds.TUNE_TABLE)
+        tuned_plan = ds.plan_histogram(n, U, w, probe["skew_class"])
+        t_tuned, H_tuned = med(keys, U, probe["skew_class"])
+        same = bool(torch.equal(H_model, H_tuned)) and int(H_tuned.to(torch.int64).sum().item()) == n
+        keep = ("regime_name", "crn", "replicas", "threads", "blocks")
+        rows.append({"U": U, "key_bytes": w, "distribution": "Zipf s=1.1" if d == "zipf" else "uniform",
+                     "probe": {k: probe[k] for k in ("skew_name", "samples", "equal_neighbours",
+                                                      "top_multiplicity")}, "probe_ms_host": round(probe_ms, 4),
+                     "cost_model": {"plan": {k: model_plan[k] for k in keep}, "ms": t_model},
+                     "tuned": {"plan": {k: tuned_plan[k] for k in keep}, "ms": t_tuned},
+                     "speedup": t_model / t_tuned, "same_histogram": same})
+        del keys, H_model, H_tuned
+        torch.cuda.empty_cache()
+    status = ds.stream_status()
+    return {"workload": f"the universe sweep: histogram (Eq. (1)) of n = 2^27 keys, median of {reps} launches "
+                        "after 2 warm-ups, keys larger than L2", "table_entries": ds.tune_table_size(),
+            "rows": rows, "tuned_never_slower": all(r["tuned"]["ms"] <= r["cost_model"]["ms"] * 1.02 for r in rows),
+            "tolerance": "2 % (launch-to-launch noise)", "all_same_histogram": all(r["same_histogram"] for r in rows),
+            "status": status}
+
+
+def run_chunked(ds, torch, stream, n: int = 1 << 28, U: int = 1 << 20, reps: int = 5):
+    """Host-resident keys sorted two ways: serial (one copy of all keys to the device, then the sort) and
+    chunked (dialsort_sort_chunked: each chunk's copy overlaps the ingestion of the chunk before; the
+    projection runs once at the end).  Same keys, same output buffer on the device, events on `stream`."""
+    import gen
+
+    host = gen.keys(n, U, "uniform", stream=SEED_STREAM)
+    pin = torch.from_numpy(host.view(np.int32)).pin_memory()
+    del host
+    d_keys = torch.empty(n, dtype=torch.int32, device="cuda")
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    ws = torch.empty(ds.sort_workspace_size(n, U), dtype=torch.uint8, device="cuda")
+    cs = torch.cuda.Stream()
+    cws = {}
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ts.sort()
+        return ts[len(ts) // 2]
+
+    def copy_only():
+        with torch.cuda.stream(stream):
+            d_keys.copy_(pin, non_blocking=True)
+
+    def sort_only():
+        ds.sort(d_keys, U, out=out, ws=ws, stream=stream)
+
+    def serial():
+        copy_only()
+        sort_only()
+
+    t_copy, t_sort, t_serial = timed(copy_only), timed(sort_only), timed(serial)
+    ref = out.clone()
+    rows = []
+    for chunk in (1 << 22, 1 << 24, 1 << 26):
+        need = ds.lib().dialsort_chunked_workspace_size(n, U, 4, chunk, 1)
+        cws[chunk] = torch.empty(need, dtype=torch.uint8, device="cuda")
+        out.fill_(-1)
+        t = timed(lambda: ds.sort_chunked(pin, U, out, chunk_keys=chunk, ws=cws[chunk], stream=stream,
+                                          copy_stream=cs))
+        rows.append({"chunk_keys": chunk, "ms": t, "keys_per_s": n / (t / 1e3), "same_output": bool(torch.equal(out, ref))})
+        del cws[chunk]
+    best = min(rows, key=lambda r: r["ms"])
+    status = ds.stream_status()
+    return {"workload": f"dialsort_sort of n = 2^28 uint32 keys, U = 2^20, uniform, in page-locked host memory "
+                        f"(1 GiB), output on the device; median of {reps}",
+            "copy_ms": t_copy, "device_sort_ms": t_sort, "serial_ms": t_serial,
+            "serial_keys_per_s": n / (t_serial / 1e3), "chunked": rows, "best_chunked_ms": best["ms"],
+            "saved_ms": t_serial - best["ms"], "lower_bound_ms": max(t_copy, t_sort),
+            "how": "serial: one cudaMemcpyAsync of all keys, then dialsort_sort; chunked: dialsort_sort_chunked with "
+                   "two staging buffers, copies on a second stream", "status": status}
+
+
 def run_batched(ds, torch, stream, reps: int = 3):
     """4096 independent instances in one persistent launch vs per-request plain launches.
 
@@ -563,6 +689,10 @@ def main():
             res = run_radix(ds, torch, stream, n=args.n)
         elif args.form == "paper":
             res = run_paper(ds, torch, stream)
+        elif args.form == "autotune":
+            res = run_autotune(ds, torch, stream)
+        elif args.form == "chunked":
+            res = run_chunked(ds, torch, stream)
         else:
             res = run_served(ds, torch, seconds=args.served_seconds)
         print(json.dumps({"form": args.form, **res}), flush=True)
@@ -785,6 +915,13 @@ def main():
             forms["paper_grid"] = run_paper(ds, torch, stream)
         except Exception as exc:
             forms["paper_grid"] = {"unavailable": str(exc)[:200]}
+        torch.cuda.empty_cache()
+        try:
+            forms["autotune"] = run_autotune(ds, torch, stream)
+        except Exception as exc:
+            forms["autotune"] = {"unavailable": str(exc)[:200]}
+        torch.cuda.empty_cache()
+        forms["chunked_ingest"] = run_chunked(ds, torch, stream)
         torch.cuda.empty_cache()
 
     if rank == 0:

@@ -78,6 +78,17 @@ typedef enum {
                                      16-byte aligned) */
 } dialsort_regime_t;
 
+/* Skew classes of a key sequence (dialsort_probe_skew; the autotuner's table
+ * is keyed by them).  How often equal keys meet decides what the CRN's merge
+ * saves and how contended the counters get (Sec. "Conflict Resolution
+ * Network", the remark on skewed inputs). */
+typedef enum {
+  DIALSORT_SKEW_UNKNOWN = 0,
+  DIALSORT_SKEW_LOW = 1,    /* few equal keys meet: near uniform over a large universe */
+  DIALSORT_SKEW_HOT = 2,    /* a few keys hold a large share (Zipf-like) */
+  DIALSORT_SKEW_RUNS = 3,   /* most neighbours are equal (sorted input, long runs, all equal) */
+} dialsort_skew_class_t;
+
 /* Launch choices for step 1.  Zero in any field means "pick automatically". */
 typedef struct {
   uint32_t regime;   /* dialsort_regime_t */
@@ -87,6 +98,8 @@ typedef struct {
   uint32_t threads;  /* CTA size: 256, 512 or 1024 */
   uint32_t replicas; /* shared-memory sub-histogram copies per CTA (SMEM32 / SMEM16) */
   uint32_t cluster;  /* CTAs per cluster (CLUSTER regime): 2, 4, 8 or 16 */
+  uint32_t skew;     /* dialsort_skew_class_t of the keys, when known: with every other field zero the
+                        autotuner takes its measured table's entry for this class (0 = unknown) */
 } dialsort_hist_config_t;
 
 /* ---------------------------------------------------------------- step 1: ingestion, Eq. (1) */
@@ -141,16 +154,89 @@ dialsort_status_t dialsort_histogram_accumulate(const void* keys, uint32_t key_b
                                                uint32_t* H, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * Chunked ingestion from host memory, overlapped with the copies: the
+ * streaming form of Eq. (1) (the remark after Thm. "Parallel DialSort with
+ * pipelined CRN": H is a sum over keys, so it can absorb each batch as it
+ * lands).  host_keys (n keys of key_bytes = 4 or 2; page-locked host memory,
+ * else the copies do not overlap) is copied chunk_keys keys at a time into
+ * two device staging buffers in ws on copy_stream, while `stream` ingests
+ * the previous chunk into H; a staging buffer is refilled only once the
+ * ingestion that read it has finished.  Both streams must be distinct and
+ * non-NULL; the copies first wait for the work already queued on `stream`.
+ *   dialsort_histogram_chunked: H (device, U counters, 16-byte aligned)
+ *     += histogram of the keys (H must hold valid counts: zero it once first,
+ *     as for dialsort_histogram_accumulate).
+ *   dialsort_sort_chunked: H in ws from 0, then Eq. (2) into out (device or
+ *     page-locked host memory, n keys) on `stream`.
+ * ws: device memory, 256-byte aligned, dialsort_chunked_workspace_size bytes
+ * (sort != 0 for the sort).  Asynchronous; kernel-side errors go to the
+ * error word.
+ */
+size_t dialsort_chunked_workspace_size(uint64_t n, uint32_t U, uint32_t key_bytes, uint64_t chunk_keys, int sort);
+dialsort_status_t dialsort_histogram_chunked(const void* host_keys, uint32_t key_bytes, uint64_t n, uint32_t U,
+                                             uint64_t chunk_keys, uint32_t* H, void* ws, size_t ws_bytes,
+                                             void* stream, void* copy_stream);
+dialsort_status_t dialsort_sort_chunked(const void* host_keys, uint32_t key_bytes, uint64_t n, uint32_t U,
+                                        uint64_t chunk_keys, void* out, void* ws, size_t ws_bytes, void* stream,
+                                        void* copy_stream);
+
+/*
  * The autotuner's choice for a histogram of n keys of key_bytes over [0,U)
- * with the given skew hint (0 = unknown, 1 = low conflict, 2 = skewed).
- * Host only; writes *cfg with every field filled in.  With cfg->regime AUTO
+ * with the given skew hint (a dialsort_skew_class_t, 0..3).  Host only;
+ * writes *cfg with every field filled in.  With every field of *cfg zero on
+ * input the choice comes from the measured tuning table (see
+ * dialsort_tune_table_load) when it has an entry near (n, U) for this key
+ * width and skew class, else from the built-in cost model.  With regime AUTO
  * on input, DIALSORT_REGIME_TWO_LEVEL is reported where dialsort_histogram_ws
  * and dialsort_sort choose it (16-byte aligned keys, workspace given); the
- * other fields then describe the single-pass L2 plan that dialsort_histogram
+ * other fields then describe the single-pass plan that dialsort_histogram
  * (no workspace) runs instead.
  */
 dialsort_status_t dialsort_plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
                                           dialsort_hist_config_t* cfg);
+
+/* What the skew probe saw (dialsort_probe_skew). */
+typedef struct {
+  uint32_t samples;          /* sampled keys below U */
+  uint32_t equal_neighbours; /* sampled neighbour pairs holding equal keys */
+  uint32_t neighbour_pairs;  /* sampled neighbour pairs */
+  uint32_t top_multiplicity; /* largest count of one key among the samples */
+  uint32_t skew_class;       /* dialsort_skew_class_t derived from the above */
+  uint32_t reserved;
+} dialsort_skew_t;
+
+/*
+ * Skew probe: one CTA reads 128 windows of 32 consecutive keys spread evenly
+ * over keys[0..n) (4096 keys; fewer when n is small) and measures, with
+ * equality tests between keys only (Definition "Order comparison"), how many
+ * neighbours are equal and the largest multiplicity of one key (a hash table
+ * in shared memory whose probes compare keys for equality).  The class is
+ * RUNS when at least half of the neighbour pairs are equal, HOT when one key
+ * holds at least max(4 x samples / U, samples / 64) samples, else LOW;
+ * UNKNOWN below 64 samples.  keys: device (or page-locked host) memory,
+ * key_bytes 4 or 2, aligned to its width.  Synchronous: waits for `stream`
+ * and fills *out.  Keys >= U are not counted (and raise no error).
+ */
+dialsort_status_t dialsort_probe_skew(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U,
+                                      dialsort_skew_t* out, void* stream);
+
+/*
+ * The tuning table: text lines "log2n log2U key_bytes skew regime crn
+ * replicas threads blocks_per_sm" ('#' starts a comment; crn in the
+ * dialsort_hist_config_t coding; 0 in a field = automatic), measured on the
+ * device by the package's tuning script.  The planner takes the entry with
+ * the same key width and skew class nearest to (log2 n, log2 U), distance
+ * 2|dU| + |dn| at most 6, and uses the cost model where there is none or
+ * the entry does not apply (e.g. TWO_LEVEL without workspace).  Loaded at
+ * the first plan from the file named by the environment variable
+ * DIALSORT_TUNE_CACHE (set but empty: no table), else from tune_table.txt in
+ * the library's directory.  dialsort_tune_table_load replaces the table by
+ * the file at `path` (NULL: an empty table, the cost model alone); an
+ * unreadable file returns INVALID_ARG and keeps the old table.
+ */
+dialsort_status_t dialsort_tune_table_load(const char* path);
+/* Number of entries in the table in use (loads it first if needed). */
+uint32_t dialsort_tune_table_size(void);
 
 /* ---------------------------------------------------------------- step 2: ordered projection, Eq. (2) */
 
@@ -228,6 +314,13 @@ dialsort_status_t dialsort_sort(const uint32_t* keys, uint64_t n, uint32_t U, ui
                                 size_t ws_bytes, void* stream);
 dialsort_status_t dialsort_sort_u16(const uint16_t* keys, uint64_t n, uint32_t U, uint16_t* out, void* ws,
                                     size_t ws_bytes, void* stream);
+/*
+ * As dialsort_sort (key_bytes 4 or 2) with explicit launch choices for step 1
+ * (cfg as for dialsort_histogram_ws, NULL = automatic; its skew field feeds
+ * the autotuner).  ws as for dialsort_sort.
+ */
+dialsort_status_t dialsort_sort_ex(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, void* out,
+                                   const dialsort_hist_config_t* cfg, void* ws, size_t ws_bytes, void* stream);
 /* Device pointer to the histogram that dialsort_sort leaves in ws. */
 uint32_t* dialsort_sort_histogram(void* ws);
 
@@ -324,7 +417,15 @@ typedef struct {
   uint64_t n;
   uint32_t U;
   uint32_t key_bytes;
+  uint32_t skew;     /* dialsort_skew_class_t of the keys, 0 = unknown (dialsort_probe_skew_batched) */
+  uint32_t reserved; /* 0 */
 } dialsort_instance_t;
+
+/*
+ * The skew probe of dialsort_probe_skew for every instance of an array in one
+ * launch (one CTA per instance); writes instances[i].skew.  Synchronous.
+ */
+dialsort_status_t dialsort_probe_skew_batched(dialsort_instance_t* instances, uint32_t count, void* stream);
 
 /* A planned batch (host object).  Planning picks, per instance, how step 1
  * privatises H (shared-memory 32-bit, packed 16-bit, or L2 atomics with the
@@ -387,7 +488,7 @@ typedef struct {
   uint32_t U;
   uint32_t key_bytes; /* 4 or 2 */
   uint32_t kind;      /* 0 = histogram (step 1), 1 = sort (steps 1 and 2) */
-  uint32_t reserved;
+  uint32_t skew;      /* dialsort_skew_class_t of the keys if known, else 0 */
 } dialsort_request_t;
 
 /* A finished request.  H (U counters) and out (n sorted keys, kind 1 only)

@@ -12,6 +12,7 @@ values held in torch.int32 tensors.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import torch
 
@@ -21,13 +22,17 @@ __all__ = [
     "DialSortError", "histogram", "reconstruct", "sort", "offsets", "plan_histogram", "stream_status",
     "sort_workspace_size", "reconstruct_workspace_size", "REGIMES", "lib", "Batch", "batched", "Server",
     "replay", "device_view", "pageable_host_access", "histogram_accumulate", "frequency", "presence",
-    "range_count", "radix_sort", "sort_mapped",
+    "range_count", "radix_sort", "sort_mapped", "probe_skew", "tune_table_load", "tune_table_size",
+    "SKEW_CLASSES", "histogram_chunked", "sort_chunked",
 ]
 
 OK, ERR_INVALID_ARG, ERR_KEY_RANGE, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_BUSY, ERR_OVERFLOW, ERR_WORKSPACE = range(9)
 
 REGIMES = {"auto": 0, "smem32": 1, "smem16": 2, "cluster": 3, "global_crn": 4, "global": 5, "two_level": 6}
 REGIME_NAMES = {v: k for k, v in REGIMES.items()}
+# skew classes (dialsort_skew_class_t): what the skew probe reports and the tuning table is keyed by
+SKEW_CLASSES = {"unknown": 0, "low": 1, "hot": 2, "runs": 3}
+SKEW_NAMES = {v: k for k, v in SKEW_CLASSES.items()}
 
 _W4 = (torch.int32, torch.uint32)
 _W2 = (torch.int16, torch.uint16)
@@ -74,7 +79,7 @@ def _cuda(t: torch.Tensor, name: str) -> torch.Tensor:
 
 def _reachable(t: torch.Tensor, name: str) -> torch.Tensor:
     """A CUDA tensor, or a page-locked host tensor that the kernels read or write over the host link."""
-    if not (t.is_cuda or t.is_pinned()):
+    if not (t.is_cuda or t.is_pinned() or t.numel() == 0):  # (an empty tensor holds no pages to pin)
         raise ValueError(f"{name} must be a CUDA tensor or pinned host memory (DialSort has no CPU path)")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
@@ -100,7 +105,44 @@ def _config(config) -> ctypes.c_void_p | None:
             v = 1 if v else 2
         if k == "crn" and v == "adaptive":
             v = 3
+        if k == "skew" and isinstance(v, str):
+            v = SKEW_CLASSES[v]
         setattr(c, k, int(v))
+    return c
+
+
+def probe_skew(keys: torch.Tensor, U: int, stream=None) -> dict:
+    """The device skew probe (4096 sampled keys, equality tests only): counts and the skew class."""
+    _reachable(keys, "keys")
+    r = native.dialsort_skew_t()
+    _check(native.load().dialsort_probe_skew(keys.data_ptr(), _width(keys), keys.numel(), U, ctypes.byref(r),
+                                             _stream(stream)), "dialsort_probe_skew")
+    d = {f: getattr(r, f) for f, _ in r._fields_ if f != "reserved"}
+    d["skew_name"] = SKEW_NAMES[d["skew_class"]]
+    return d
+
+
+# the table the library loads when DIALSORT_TUNE_CACHE is not set (written by python -m paper_2605_16667_gb300.tune)
+TUNE_TABLE = os.path.join(os.path.dirname(native.LIB_PATH), "tune_table.txt")
+
+
+def tune_table_load(path: str | None) -> None:
+    """Replace the autotuner's measured table by the file at path (None: no table, the cost model alone)."""
+    _check(native.load().dialsort_tune_table_load(path.encode() if path is not None else None), "tune_table_load")
+
+
+def tune_table_size() -> int:
+    return int(native.load().dialsort_tune_table_size())
+
+
+def _with_skew(config, skew, keys, U, stream):
+    """config with the skew class set: an int or name, or "probe" to run the skew probe first."""
+    if skew is None:
+        return config
+    if skew == "probe":
+        skew = probe_skew(keys, U, stream)["skew_class"]
+    c = dict(config or {})
+    c["skew"] = SKEW_CLASSES[skew] if isinstance(skew, str) else int(skew)
     return c
 
 
@@ -109,18 +151,19 @@ def histogram_workspace_size(n: int, U: int, width: int = 4) -> int:
 
 
 def histogram(keys: torch.Tensor, U: int, H: torch.Tensor | None = None, *, config: dict | None = None,
-              ws: torch.Tensor | None = None, use_workspace: bool = True, stream=None) -> torch.Tensor:
+              ws: torch.Tensor | None = None, use_workspace: bool = True, stream=None, skew=None) -> torch.Tensor:
     """Eq. (1): H[k] = number of keys equal to k, for k in [0, U).  Returns H (int32 storage of uint32).
 
     With use_workspace (default) a workspace is passed, so large universes can use the two-level regime.
-    keys may be pinned host memory: the kernels then read it over the host link.
+    keys may be pinned host memory: the kernels then read it over the host link.  skew: the keys' skew
+    class for the autotuner (a SKEW_CLASSES name or number, or "probe" to measure it first).
     """
     _reachable(keys, "keys")
     w = _width(keys)
     if H is None:
         H = torch.empty(U, dtype=torch.int32, device=_device(keys))
     _reachable(H, "H")
-    cfg = _config(config)
+    cfg = _config(_with_skew(config, skew, keys, U, stream))
     L = native.load()
     need = histogram_workspace_size(keys.numel(), U, w) if use_workspace else 0
     if need:
@@ -179,11 +222,12 @@ def offsets(H: torch.Tensor, U: int, n: int, *, ws: torch.Tensor | None = None, 
 
 
 def sort(keys: torch.Tensor, U: int, out: torch.Tensor | None = None, *, ws: torch.Tensor | None = None,
-         stream=None, return_histogram: bool = False):
+         stream=None, return_histogram: bool = False, config: dict | None = None, skew=None):
     """Eq. (1) then Eq. (2).  out may be keys itself (in place).
 
     keys and out may be pinned host memory: the kernels then read the keys and write the output over
-    the host link (no staging copies); the workspace is device memory either way.
+    the host link (no staging copies); the workspace is device memory either way.  config / skew: step 1's
+    launch choices and the keys' skew class, as for histogram().
     """
     _reachable(keys, "keys")
     w = _width(keys)
@@ -196,8 +240,13 @@ def sort(keys: torch.Tensor, U: int, out: torch.Tensor | None = None, *, ws: tor
     nbytes = sort_workspace_size(n, U)
     ws = _workspace(nbytes, _device(keys), ws)
     L = native.load()
-    fn = L.dialsort_sort if w == 4 else L.dialsort_sort_u16
-    _check(fn(keys.data_ptr(), n, U, out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "dialsort_sort")
+    cfg = _config(_with_skew(config, skew, keys, U, stream))
+    if cfg is not None:
+        _check(L.dialsort_sort_ex(keys.data_ptr(), w, n, U, out.data_ptr(), ctypes.byref(cfg), ws.data_ptr(),
+                                  ws.numel(), _stream(stream)), "dialsort_sort_ex")
+    else:
+        fn = L.dialsort_sort if w == 4 else L.dialsort_sort_u16
+        _check(fn(keys.data_ptr(), n, U, out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "dialsort_sort")
     if return_histogram:
         return out, ws[: 4 * U].view(torch.int32)
     return out
@@ -215,6 +264,48 @@ def histogram_accumulate(keys: torch.Tensor, U: int, H: torch.Tensor, *, ws: tor
         keys.data_ptr(), w, keys.numel(), U, H.data_ptr(), ws.data_ptr() if ws is not None else None,
         ws.numel() if ws is not None else 0, _stream(stream)), "dialsort_histogram_accumulate")
     return H
+
+
+def _host_keys(keys: torch.Tensor):
+    if keys.is_cuda:
+        raise TypeError("keys must be host memory (page-locked for the copies to overlap)")
+    if not keys.is_contiguous():
+        raise TypeError("keys must be contiguous")
+    return _width(keys)
+
+
+def histogram_chunked(keys: torch.Tensor, U: int, H: torch.Tensor, *, chunk_keys: int = 1 << 24,
+                      ws: torch.Tensor | None = None, stream=None, copy_stream=None) -> torch.Tensor:
+    """Eq. (1) streamed from host memory: H += histogram of keys, chunk by chunk, each chunk's copy to the
+    device overlapping the ingestion of the one before (copy_stream: a second CUDA stream)."""
+    w = _host_keys(keys)
+    _cuda(H, "H")
+    L = native.load()
+    need = L.dialsort_chunked_workspace_size(keys.numel(), U, w, chunk_keys, 0)
+    ws = _workspace(need, H.device, ws)
+    cs = copy_stream if copy_stream is not None else torch.cuda.Stream(device=H.device)
+    _check(L.dialsort_histogram_chunked(keys.data_ptr(), w, keys.numel(), U, chunk_keys, H.data_ptr(),
+                                        ws.data_ptr(), ws.numel(), _stream(stream), _stream(cs)),
+           "dialsort_histogram_chunked")
+    return H
+
+
+def sort_chunked(keys: torch.Tensor, U: int, out: torch.Tensor | None = None, *, chunk_keys: int = 1 << 24,
+                 ws: torch.Tensor | None = None, stream=None, copy_stream=None, device=None) -> torch.Tensor:
+    """Sort host-resident keys: the chunked, copy-overlapped ingestion, then Eq. (2) into out (device by
+    default, or page-locked host memory)."""
+    w = _host_keys(keys)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        out = torch.empty(keys.numel(), dtype=keys.dtype, device=dev)
+    _reachable(out, "out")
+    L = native.load()
+    need = L.dialsort_chunked_workspace_size(keys.numel(), U, w, chunk_keys, 1)
+    ws = _workspace(need, dev, ws)
+    cs = copy_stream if copy_stream is not None else torch.cuda.Stream(device=dev)
+    _check(L.dialsort_sort_chunked(keys.data_ptr(), w, keys.numel(), U, chunk_keys, out.data_ptr(), ws.data_ptr(),
+                                   ws.numel(), _stream(stream), _stream(cs)), "dialsort_sort_chunked")
+    return out
 
 
 _W1 = (torch.uint8, torch.int8)
@@ -346,7 +437,7 @@ class Batch:
     tensors (allocated when None); out: list of output tensors (allocated when sort and None).
     """
 
-    def __init__(self, keys, U, H=None, out=None, *, sort: bool = True):
+    def __init__(self, keys, U, H=None, out=None, *, sort: bool = True, skew=None):
         L = native.load()
         n = len(keys)
         self.keys = list(keys)
@@ -368,6 +459,11 @@ class Batch:
             arr[i].n = self.keys[i].numel()
             arr[i].U = self.U[i]
             arr[i].key_bytes = _width(self.keys[i])
+            if skew is not None and skew != "probe":
+                arr[i].skew = SKEW_CLASSES[skew[i]] if isinstance(skew[i], str) else int(skew[i])
+        if skew == "probe" and n:  # one probe launch for every instance
+            _check(L.dialsort_probe_skew_batched(arr, n, _stream(None)), "probe_skew_batched")
+        self.skew = [arr[i].skew for i in range(n)]
         self._handle = ctypes.c_void_p()
         _check(L.dialsort_batch_create(arr, n, 1 if self.sort else 0, ctypes.byref(self._handle)), "batch_create")
         self.ws = torch.empty(max(L.dialsort_batch_workspace_size(self._handle), 256), dtype=torch.uint8,
@@ -382,7 +478,8 @@ class Batch:
         c = native.dialsort_hist_config_t()
         items = (ctypes.c_uint32 * 4)()
         _check(native.load().dialsort_batch_describe(self._handle, i, ctypes.byref(c), items), "batch_describe")
-        return {"regime_name": REGIME_NAMES[c.regime], "replicas": c.replicas, "items": list(items)}
+        return {"regime_name": REGIME_NAMES[c.regime], "replicas": c.replicas, "items": list(items),
+                "crn": {1: "on", 2: "off", 3: "adaptive"}[c.crn], "skew": SKEW_NAMES[self.skew[i]]}
 
     def close(self):
         if self._handle:
@@ -429,9 +526,10 @@ class Server:
         _check(native.load().dialsort_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "server_create")
         self._keep = {}
 
-    def submit(self, keys: torch.Tensor, U: int, kind: str = "sort") -> int:
+    def submit(self, keys: torch.Tensor, U: int, kind: str = "sort", skew=0) -> int:
         _cuda(keys, "keys")
-        r = native.dialsort_request_t(keys.data_ptr(), keys.numel(), U, _width(keys), 1 if kind == "sort" else 0, 0)
+        sk = SKEW_CLASSES[skew] if isinstance(skew, str) else int(skew)
+        r = native.dialsort_request_t(keys.data_ptr(), keys.numel(), U, _width(keys), 1 if kind == "sort" else 0, sk)
         t = ctypes.c_uint64()
         _check(native.load().dialsort_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "server_submit")
         self._keep[t.value] = (keys, U, kind)  # keys must stay alive until the request finishes

@@ -70,7 +70,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if err.strip():
                 print(f"== {os.path.basename(obj)}\n{err}")
     tmp = LIB + ".tmp"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

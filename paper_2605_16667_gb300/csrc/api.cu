@@ -147,12 +147,17 @@ dialsort_status_t histogram_impl(const void* keys, uint32_t key_bytes, uint64_t 
   keys = kp;
   H = static_cast<uint32_t*>(const_cast<void*>(hp));
   HistPlan plan;
-  s = plan_histogram(n, U, key_bytes, 0, cfg, *dev, &plan);
+  const uint32_t skew = cfg ? cfg->skew : 0u;
+  s = plan_histogram(n, U, key_bytes, skew, cfg, *dev, &plan);
   if (s != DIALSORT_OK) return s;
-  // large universes: the two-level regime when it applies and the workspace holds its scratch
-  const bool forced = plan.regime == DIALSORT_REGIME_TWO_LEVEL;
+  // large universes: the two-level regime when it applies and the workspace holds its scratch: where
+  // the tuning table names it, or (no table entry) for every shape where the cost model's L2 plan would
+  // run.  A measured single-pass entry stands.
+  const bool forced = plan.regime == DIALSORT_REGIME_TWO_LEVEL && !plan.tuned;
   const bool auto_large = (cfg == nullptr || cfg->regime == DIALSORT_REGIME_AUTO) &&
-                          (plan.regime == DIALSORT_REGIME_GLOBAL_CRN || plan.regime == DIALSORT_REGIME_GLOBAL);
+                          (plan.tuned ? plan.regime == DIALSORT_REGIME_TWO_LEVEL
+                                      : (plan.regime == DIALSORT_REGIME_GLOBAL_CRN ||
+                                         plan.regime == DIALSORT_REGIME_GLOBAL));
   // the two-level passes read device memory (the U > 2^21 form moves keys with bulk (TMA) copies)
   if ((forced || auto_large) && !keys_in_host && hier_fits(n, U, key_bytes, keys)) {
     const HierLayout T = hier_layout(n, U);
@@ -168,6 +173,11 @@ dialsort_status_t histogram_impl(const void* keys, uint32_t key_bytes, uint64_t 
   } else if (forced) {
     return DIALSORT_ERR_INVALID_ARG;
   }
+  // a tuned two-level entry without its workspace: the cost model's single-pass plan
+  if (plan.regime == DIALSORT_REGIME_TWO_LEVEL &&
+      (s = plan_histogram(n, U, key_bytes, skew, cfg, *dev, &plan, false)) != DIALSORT_OK)
+    return s;
+  if (plan.regime == DIALSORT_REGIME_TWO_LEVEL) return DIALSORT_ERR_INVALID_ARG;
   // Eq. (1) starts from H = 0: the Theta(U) initialisation (skipped when accumulating into H)
   cudaError_t e = accumulate ? cudaSuccess : cudaMemsetAsync(H, 0, (size_t)U * 4, st);
   if (e == cudaSuccess && n > 0) e = launch_histogram(keys, key_bytes, n, U, H, plan, dev->err, st);
@@ -197,7 +207,7 @@ size_t sort_h_bytes(uint32_t U) { return align_up((size_t)U * 4, 256); }
 
 // sort workspace: H | reconstruction scratch | ingestion scratch
 dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, void* out, void* ws,
-                            size_t ws_bytes, cudaStream_t st) {
+                            size_t ws_bytes, cudaStream_t st, const dialsort_hist_config_t* cfg = nullptr) {
   dialsort_status_t s = check_keys(keys, key_bytes, n, U);
   if (s != DIALSORT_OK) return s;
   if (n > 0 && (out == nullptr || !aligned(out, key_bytes))) return DIALSORT_ERR_INVALID_ARG;
@@ -205,7 +215,9 @@ dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, ui
   if (ws == nullptr || !aligned(ws, 256) || ws_bytes < hb + rb + ib) return DIALSORT_ERR_WORKSPACE;
   char* base = static_cast<char*>(ws);
   uint32_t* H = reinterpret_cast<uint32_t*>(base);
-  if (small_sort_fits(n, U, key_bytes)) {
+  const bool auto_cfg = cfg == nullptr || (cfg->regime == 0 && cfg->crn == 0 && cfg->blocks == 0 &&
+                                            cfg->threads == 0 && cfg->replicas == 0 && cfg->cluster == 0);
+  if (auto_cfg && small_sort_fits(n, U, key_bytes)) {
     // a small input: the whole sort in one launch
     const DeviceInfo* dev = device_info();
     if (!dev) return DIALSORT_ERR_CUDA;
@@ -215,7 +227,7 @@ dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, ui
     return from_cuda(launch_small_sort(kp, key_bytes, n, U, H, const_cast<void*>(op), base + hb, recon_layout(U, n),
                                        *dev, dev->err, st));
   }
-  s = histogram_impl(keys, key_bytes, n, U, H, nullptr, ib ? base + hb + rb : nullptr, ib, st);
+  s = histogram_impl(keys, key_bytes, n, U, H, cfg, ib ? base + hb + rb : nullptr, ib, st);
   if (s != DIALSORT_OK) return s;
   return reconstruct_impl(H, U, out, key_bytes, n, base + hb, rb, st);
 }
@@ -246,6 +258,8 @@ dialsort_status_t sort_mapped_impl(const void* keys, uint32_t key_bytes, uint64_
   if (s != DIALSORT_OK) return s;
   HistPlan plan;
   s = plan_histogram(n, U, key_bytes, 0, nullptr, *dev, &plan);
+  if (s == DIALSORT_OK && plan.regime == DIALSORT_REGIME_TWO_LEVEL)  // single-pass regimes only here
+    s = plan_histogram(n, U, key_bytes, 0, nullptr, *dev, &plan, false);
   if (s != DIALSORT_OK) return s;
   char* base = static_cast<char*>(ws);
   uint32_t* H = reinterpret_cast<uint32_t*>(base);
@@ -257,9 +271,89 @@ dialsort_status_t sort_mapped_impl(const void* keys, uint32_t key_bytes, uint64_
   return from_cuda(e);
 }
 
+// Chunked ingestion from host memory (the remark after Thm. "Parallel DialSort with pipelined CRN":
+// Eq. (1) is a sum over keys, so H can absorb keys as they arrive).  Chunk i is copied into one of two
+// device staging buffers on copy_stream while `st` accumulates chunk i - 1; staging buffer i & 1 is
+// refilled only after the accumulation of chunk i - 2 has read it.  Workspace: staging[2] | ingestion
+// scratch of one chunk | (sort) H | projection scratch.
+struct ChunkedLayout {
+  size_t stage, ingest, h, recon, total;
+};
+
+ChunkedLayout chunked_layout(uint64_t n, uint32_t U, uint32_t key_bytes, uint64_t chunk, bool sort) {
+  ChunkedLayout L{};
+  L.stage = align_up((size_t)std::min<uint64_t>(chunk, std::max<uint64_t>(n, 1)) * key_bytes, 256);
+  L.ingest = hist_ws_bytes(std::min(chunk, n), U, key_bytes);
+  L.h = sort ? sort_h_bytes(U) : 0;
+  L.recon = sort ? recon_layout(U, n).total : 0;
+  L.total = 2 * L.stage + L.ingest + L.h + L.recon;
+  return L;
+}
+
+dialsort_status_t chunked_impl(const void* host_keys, uint32_t key_bytes, uint64_t n, uint32_t U, uint64_t chunk,
+                               uint32_t* H, void* out, void* ws, size_t ws_bytes, cudaStream_t st,
+                               cudaStream_t cs, bool sort) {
+  dialsort_status_t s = check_keys(host_keys, key_bytes, n, U);
+  if (s != DIALSORT_OK) return s;
+  if (chunk == 0 || cs == nullptr || cs == st) return DIALSORT_ERR_INVALID_ARG;
+  if (sort && n > 0 && (out == nullptr || !aligned(out, key_bytes))) return DIALSORT_ERR_INVALID_ARG;
+  const ChunkedLayout L = chunked_layout(n, U, key_bytes, chunk, sort);
+  if (ws == nullptr || !aligned(ws, 256) || ws_bytes < L.total) return DIALSORT_ERR_WORKSPACE;
+  char* base = static_cast<char*>(ws);
+  char* stage[2] = {base, base + L.stage};
+  void* ingest = L.ingest ? base + 2 * L.stage : nullptr;
+  if (sort) H = reinterpret_cast<uint32_t*>(base + 2 * L.stage + L.ingest);
+  if (H == nullptr || !aligned(H, 16)) return DIALSORT_ERR_INVALID_ARG;
+  cudaError_t e = cudaSuccess;
+  if (sort) e = cudaMemsetAsync(H, 0, (size_t)U * 4, st);  // Eq. (1) starts from H = 0
+  cudaEvent_t ev[5] = {};  // entry, copied[2], consumed[2]
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+  // the copies start after the work already queued on `st` (earlier users of the workspace)
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+  const char* src = static_cast<const char*>(host_keys);
+  const uint64_t chunks = (n + chunk - 1) / chunk;
+  for (uint64_t i = 0; i < chunks && e == cudaSuccess && s == DIALSORT_OK; ++i) {
+    const int slot = (int)(i & 1);
+    const uint64_t len = std::min(chunk, n - i * chunk);
+    if (i >= 2) e = cudaStreamWaitEvent(cs, ev[3 + slot], 0);  // chunk i - 2 has been ingested
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(stage[slot], src + i * chunk * key_bytes, len * key_bytes, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + slot], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1 + slot], 0);
+    if (e != cudaSuccess) break;
+    s = histogram_impl(stage[slot], key_bytes, len, U, H, nullptr, ingest, L.ingest, st, true);
+    if (s == DIALSORT_OK) e = cudaEventRecord(ev[3 + slot], st);
+  }
+  for (int i = 0; i < 5; ++i)
+    if (ev[i]) (void)cudaEventDestroy(ev[i]);  // released once the recorded work has completed
+  if (e != cudaSuccess) return from_cuda(e);
+  if (s != DIALSORT_OK || !sort) return s;
+  return reconstruct_impl(H, U, out, key_bytes, n, base + 2 * L.stage + L.ingest + L.h, L.recon, st);
+}
+
 }  // namespace
 
 extern "C" {
+
+size_t dialsort_chunked_workspace_size(uint64_t n, uint32_t U, uint32_t key_bytes, uint64_t chunk_keys, int sort) {
+  if (chunk_keys == 0 || (key_bytes != 4 && key_bytes != 2)) return 0;
+  return chunked_layout(n, U, key_bytes, chunk_keys, sort != 0).total;
+}
+
+dialsort_status_t dialsort_histogram_chunked(const void* host_keys, uint32_t key_bytes, uint64_t n, uint32_t U,
+                                             uint64_t chunk_keys, uint32_t* H, void* ws, size_t ws_bytes,
+                                             void* stream, void* copy_stream) {
+  return chunked_impl(host_keys, key_bytes, n, U, chunk_keys, H, nullptr, ws, ws_bytes, as_stream(stream),
+                      static_cast<cudaStream_t>(copy_stream), false);
+}
+
+dialsort_status_t dialsort_sort_chunked(const void* host_keys, uint32_t key_bytes, uint64_t n, uint32_t U,
+                                        uint64_t chunk_keys, void* out, void* ws, size_t ws_bytes, void* stream,
+                                        void* copy_stream) {
+  return chunked_impl(host_keys, key_bytes, n, U, chunk_keys, nullptr, out, ws, ws_bytes, as_stream(stream),
+                      static_cast<cudaStream_t>(copy_stream), true);
+}
 
 size_t dialsort_sort_mapped_workspace_size(uint64_t n, uint32_t U) { return sort_h_bytes(U) + recon_layout(U, n).total; }
 
@@ -318,7 +412,7 @@ dialsort_status_t dialsort_histogram_ws(const void* keys, uint32_t key_bytes, ui
 
 dialsort_status_t dialsort_plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
                                           dialsort_hist_config_t* cfg) {
-  if (cfg == nullptr || U == 0 || (key_bytes != 4 && key_bytes != 2) || skew_hint > 2)
+  if (cfg == nullptr || U == 0 || (key_bytes != 4 && key_bytes != 2) || skew_hint > 3)
     return DIALSORT_ERR_INVALID_ARG;
   DeviceInfo fallback;  // planning works without a device (152 SMs, 227 KB)
   const DeviceInfo* dev = device_info();
@@ -329,11 +423,11 @@ dialsort_status_t dialsort_plan_histogram(uint64_t n, uint32_t U, uint32_t key_b
   const uint32_t crn_cfg = p.crn == 1 ? 1u : p.crn == 0 ? 2u : 3u;
   uint32_t regime = p.regime;
   // what dialsort_histogram_ws does with aligned keys and a large enough workspace
-  if (in.regime == DIALSORT_REGIME_AUTO &&
+  if (in.regime == DIALSORT_REGIME_AUTO && !p.tuned &&
       (regime == DIALSORT_REGIME_GLOBAL_CRN || regime == DIALSORT_REGIME_GLOBAL) &&
       (hier_shape_fits(n, U, key_bytes) || two_level_shape_fits(n, U, key_bytes)))
     regime = DIALSORT_REGIME_TWO_LEVEL;
-  *cfg = dialsort_hist_config_t{regime, crn_cfg, p.blocks, p.threads, p.replicas, p.cluster};
+  *cfg = dialsort_hist_config_t{regime, crn_cfg, p.blocks, p.threads, p.replicas, p.cluster, skew_hint};
   return DIALSORT_OK;
 }
 
@@ -380,6 +474,11 @@ dialsort_status_t dialsort_sort(const uint32_t* keys, uint64_t n, uint32_t U, ui
 dialsort_status_t dialsort_sort_u16(const uint16_t* keys, uint64_t n, uint32_t U, uint16_t* out, void* ws,
                                     size_t ws_bytes, void* stream) {
   return sort_impl(keys, 2, n, U, out, ws, ws_bytes, as_stream(stream));
+}
+
+dialsort_status_t dialsort_sort_ex(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, void* out,
+                                   const dialsort_hist_config_t* cfg, void* ws, size_t ws_bytes, void* stream) {
+  return sort_impl(keys, key_bytes, n, U, out, ws, ws_bytes, as_stream(stream), cfg);
 }
 
 uint32_t* dialsort_sort_histogram(void* ws) { return static_cast<uint32_t*>(ws); }

@@ -143,6 +143,113 @@ __device__ void run_hist(const Req& r, uint32_t item, uint32_t* sh, uint32_t* er
   }
 }
 
+// ---- two-level ingestion (see kPartKeys in engine.h)
+
+// Partition item t: the in-range keys of tile t grouped by bucket.  Counts go
+// to per-(bucket, lane) shared counters (a lane's adds never collide with its
+// warp neighbours'), an exclusive scan turns them into stage positions, and a
+// second read of the tile (an L1/L2 hit) places each key's low part.  The
+// stage is written out whole: 16 KB per tile, coalesced.
+template <typename KeyT>
+__device__ void part_item(const Req& r, uint32_t t, uint8_t* dyn, uint32_t* err, State* st) {
+  __shared__ uint32_t wsum[kThreads / 32];
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(dyn);                            // [B][32]
+  uint16_t* stage = reinterpret_cast<uint16_t*>(dyn + kMaxBuckets * 32 * 4);  // kPartKeys low parts
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, B = r.buckets, U = r.U;
+  const uint64_t base = (uint64_t)t * kPartKeys;
+  const uint32_t len = (uint32_t)(r.n - base < kPartKeys ? r.n - base : kPartKeys);
+  const KeyT* keys = static_cast<const KeyT*>(r.keys) + base;
+  const uint32_t E = B * 32u;
+  for (uint32_t i = tid; i < E; i += kThreads) cnt[i] = 0u;
+  __syncthreads();
+  bool bad = false;
+  for (uint32_t i = tid; i < len; i += kThreads) {
+    const uint32_t k = keys[i];
+    if (k < U)
+      atomicAdd(&cnt[(k >> kBucketBits) * 32u + lane], 1u);
+    else
+      bad = true;
+  }
+  if (bad) {
+    raise_error(err, ERRBIT_KEY_RANGE);
+    atomicOr(&st->err, ERRBIT_KEY_RANGE);
+  }
+  __syncthreads();
+  // exclusive scan over (bucket, lane): each thread sums a run of `per` counters
+  const uint32_t per = (E + kThreads - 1) / kThreads, i0 = min(E, tid * per), i1 = min(E, i0 + per);
+  uint32_t sum = 0;
+  for (uint32_t i = i0; i < i1; ++i) sum += cnt[i];
+  uint32_t inc = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= (uint32_t)d) inc += o;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  uint32_t before = 0, total = 0;
+  for (uint32_t w = 0; w < kThreads / 32; ++w) {
+    if (w < warp) before += wsum[w];
+    total += wsum[w];
+  }
+  uint32_t run = before + inc - sum;
+  for (uint32_t i = i0; i < i1; ++i) {
+    const uint32_t c = cnt[i];
+    cnt[i] = run;
+    run += c;
+  }
+  __syncthreads();
+  uint32_t* seg = r.seg + (uint64_t)t * B;
+  for (uint32_t b = tid; b < B; b += kThreads) {
+    const uint32_t start = cnt[b * 32u], end = b + 1 < B ? cnt[(b + 1) * 32u] : total;
+    seg[b] = start | ((end - start) << 16);
+  }
+  __syncthreads();  // every segment start read before the places move the counters
+  for (uint32_t i = tid; i < len; i += kThreads) {
+    const uint32_t k = keys[i];
+    if (k < U) stage[atomicAdd(&cnt[(k >> kBucketBits) * 32u + lane], 1u)] = (uint16_t)(k & ((1u << kBucketBits) - 1u));
+  }
+  __syncthreads();
+  const uint4* s4 = reinterpret_cast<const uint4*>(stage);
+  uint4* d4 = reinterpret_cast<uint4*>(r.low + base);
+  for (uint32_t q = tid; q < (total + 7u) / 8u; q += kThreads) d4[q] = s4[q];
+}
+
+// Histogram item of the two-level form: bucket b over tiles [t0, t1) (item =
+// g * B + b).  Each warp walks the segments of its tiles; the low parts go
+// through the same ingestion step as every other regime (per-lane run, warp
+// CRN by the request's choice) into packed 16-bit counters, which are then
+// added into H[b 2^14 ...].
+__device__ void count_item(const Req& r, uint32_t item, uint32_t* sh, uint32_t* err, State* st) {
+  const uint32_t B = r.buckets, tiles = r.count[PH_PART - 1], groups = r.count[PH_HIST - 1] / B;
+  const uint32_t b = item % B, g = item / B, lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t t0 = (uint32_t)((uint64_t)tiles * g / groups), t1 = (uint32_t)((uint64_t)tiles * (g + 1) / groups);
+  const uint32_t W = 1u << kBucketBits, Wb = min(W, r.U - b * W);
+  constexpr uint32_t kWords = (1u << kBucketBits) / 2u;
+  zero_smem(sh, kWords);
+  __syncthreads();
+  uint32_t* Hb = r.H + (uint64_t)b * W;
+  const Sink<MODE_SMEM16> s{sh, Hb, Wb, 0u};
+  uint32_t score = 0;
+  bool bad = false;
+  for (uint32_t t = t0 + warp; t < t1; t += kThreads / 32) {
+    const uint32_t sg = __ldg(r.seg + (uint64_t)t * B + b);
+    const uint32_t start = sg & 0xffffu, c = sg >> 16;
+    const uint16_t* lo = r.low + (uint64_t)t * kPartKeys + start;
+    for (uint32_t j = 0; j < c; j += 32) {  // c is warp-uniform: the warp stays together
+      const bool v = j + lane < c;
+      uint32_t k[1] = {v ? (uint32_t)lo[j + lane] : 0u};
+      ingest<1, MODE_SMEM16>(k, v, s, Wb, bad, r.crn, score);
+    }
+  }
+  if (bad) {  // cannot happen (low parts are below Wb); kept as a guard
+    raise_error(err, ERRBIT_KEY_RANGE);
+    atomicOr(&st->err, ERRBIT_KEY_RANGE);
+  }
+  __syncthreads();
+  flush_smem<MODE_SMEM16>(sh, 1, kWords, Wb, Hb, false);
+}
+
 __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
   extern __shared__ __align__(16) uint8_t dyn[];
   __shared__ uint64_t s_best[kThreads / 32];
@@ -279,8 +386,17 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
       case PH_ZERO:
         zero_item(r, item);
         break;
+      case PH_PART:
+        if (r.key_bytes == 4)
+          part_item<uint32_t>(r, item, dyn, L.err, st);
+        else
+          part_item<uint16_t>(r, item, dyn, L.err, st);
+        break;
       case PH_HIST:
-        run_hist(r, item, reinterpret_cast<uint32_t*>(dyn), L.err, st);
+        if (r.mode == MODE_TWO_LEVEL_ENG)
+          count_item(r, item, reinterpret_cast<uint32_t*>(dyn), L.err, st);
+        else
+          run_hist(r, item, reinterpret_cast<uint32_t*>(dyn), L.err, st);
         break;
       case PH_OFFS:
         offsets_group(r.H, r.U, r.n, num_chunks_of(r), item, r.desc, r.O, r.first, L.err,
@@ -333,10 +449,28 @@ void plan_request(const ReqPlanInput& in, Req* r) {
   r->n = in.n;
   r->U = in.U;
   r->key_bytes = in.key_bytes;
+  // the CRN by skew class: the tuning table's measured choice for this shape and class where it has
+  // one; else off when equal keys rarely meet, on for runs, adaptive per warp otherwise
   r->crn = CRN_ADAPTIVE;
+  dialsort_hist_config_t t;
+  uint32_t per_sm = 0;
+  if (in.skew != DIALSORT_SKEW_UNKNOWN && tuned_choice(in.n, in.U, in.key_bytes, in.skew, &t, &per_sm) && t.crn)
+    r->crn = t.crn == 1 ? CRN_ON : t.crn == 2 ? CRN_OFF : CRN_ADAPTIVE;
+  else if (in.skew == DIALSORT_SKEW_LOW)
+    r->crn = CRN_OFF;
+  else if (in.skew == DIALSORT_SKEW_RUNS)
+    r->crn = CRN_ON;
   const uint64_t cap32 = kHistSmem / 4, cap16 = 2 * (kHistSmem / 4);
   const uint64_t U = in.U, n = in.n;
-  if (n >= 2 * U && align_up(U, 4) <= cap32) {
+  // two-level: past the packed sub-histogram, up to 2^22 bins, with enough keys that one pass of
+  // partition + count beats one L2 atomic per key (the B x 2^13-word merges cost about U / 2 adds)
+  const bool two_level = U > cap16 && U <= ((uint64_t)kMaxBuckets << kBucketBits) && 2 * n >= U;
+  if (two_level) {
+    r->mode = MODE_TWO_LEVEL_ENG;
+    r->buckets = (uint32_t)((U + (1u << kBucketBits) - 1) >> kBucketBits);
+    r->words_per_copy = (1u << kBucketBits) / 2u;
+    r->replicas = 1;
+  } else if (n >= 2 * U && align_up(U, 4) <= cap32) {
     r->mode = MODE_SMEM32;
     r->words_per_copy = (uint32_t)align_up(U, 4);
     uint32_t rep = 1;
@@ -351,11 +485,23 @@ void plan_request(const ReqPlanInput& in, Req* r) {
     r->words_per_copy = (uint32_t)std::min<uint64_t>(align_up(U, 4), kHistSmem / 4);  // shared hot prefix
     r->replicas = 1;
   }
-  if (r->mode == MODE_GLOBAL)
-    r->item_keys = 65536;
-  else
-    r->item_keys = align_up(std::max<uint64_t>(32768, 8ull * U * r->replicas), 8192);
-  const uint32_t n_hist = (uint32_t)((n + r->item_keys - 1) / r->item_keys);
+  uint32_t n_hist;
+  if (r->mode == MODE_TWO_LEVEL_ENG) {
+    // partition tiles, then bucket x tile-group items with about 8 x 2^14 keys each or more (the
+    // merge of a group's counters stays below 1/8 of its keys' work)
+    const uint64_t tiles = (n + kPartKeys - 1) / kPartKeys;
+    const uint64_t per_bucket = n / r->buckets;
+    const uint64_t groups = std::max<uint64_t>(1, std::min<uint64_t>(tiles, per_bucket / (8ull << kBucketBits)));
+    r->item_keys = kPartKeys;
+    r->count[PH_PART - 1] = (uint32_t)tiles;
+    n_hist = (uint32_t)(groups * r->buckets);
+  } else {
+    if (r->mode == MODE_GLOBAL)
+      r->item_keys = 65536;
+    else
+      r->item_keys = align_up(std::max<uint64_t>(32768, 8ull * U * r->replicas), 8192);
+    n_hist = (uint32_t)((n + r->item_keys - 1) / r->item_keys);
+  }
   r->owned = (r->mode == MODE_SMEM32 && n_hist == 1) ? 1u : 0u;
   r->zero_H = r->owned ? 0u : 1u;
   r->count[PH_HIST - 1] = n_hist;
@@ -375,14 +521,32 @@ void plan_request(const ReqPlanInput& in, Req* r) {
 
 // scratch of a sorting request: look-back descriptors (one per offsets group),
 // chunk offsets O[0..chunks] and the first chunk of every output tile
+namespace {
+size_t two_level_scratch_bytes(const Req& r) {
+  if (r.mode != MODE_TWO_LEVEL_ENG) return 0;
+  const uint64_t tiles = r.count[PH_PART - 1];
+  return align_up(tiles * kPartKeys * 2, 256) + align_up(tiles * r.buckets * 4, 256);
+}
+}  // namespace
+
 size_t request_scratch_bytes(const Req& r) {
   const uint64_t groups = r.count[PH_OFFS - 1], tiles = r.count[PH_EXPAND - 1];
-  if (groups == 0) return 0;
+  const size_t tl = two_level_scratch_bytes(r);
+  if (groups == 0) return tl;
   const uint64_t chunks = num_chunks_of(r);
-  return align_up(8 * groups, 256) + align_up(8 * (chunks + 1), 256) + align_up(4 * std::max<uint64_t>(tiles, 1), 256);
+  return tl + align_up(8 * groups, 256) + align_up(8 * (chunks + 1), 256) +
+         align_up(4 * std::max<uint64_t>(tiles, 1), 256);
 }
 
 void place_request_scratch(Req* r, char* base) {
+  r->low = nullptr;
+  r->seg = nullptr;
+  if (r->mode == MODE_TWO_LEVEL_ENG) {
+    const uint64_t tiles = r->count[PH_PART - 1];
+    r->low = reinterpret_cast<uint16_t*>(base);
+    r->seg = reinterpret_cast<uint32_t*>(base + align_up(tiles * kPartKeys * 2, 256));
+    base += two_level_scratch_bytes(*r);
+  }
   const uint64_t groups = r->count[PH_OFFS - 1];
   if (groups == 0) {
     r->desc = nullptr;
@@ -499,7 +663,8 @@ dialsort_status_t dialsort_batch_create(const dialsort_instance_t* inst, uint32_
   std::vector<Req> plans(count);
   std::vector<double> cost(count);
   for (uint32_t i = 0; i < count; ++i) {
-    ReqPlanInput in{inst[i].keys, inst[i].H, sort ? inst[i].out : nullptr, inst[i].n, inst[i].U, inst[i].key_bytes};
+    ReqPlanInput in{inst[i].keys, inst[i].H,  sort ? inst[i].out : nullptr, inst[i].n,
+                    inst[i].U,    inst[i].key_bytes, inst[i].skew <= 3 ? inst[i].skew : 0u};
     plan_request(in, &plans[i]);
     cost[i] = (double)inst[i].n * inst[i].key_bytes * (sort ? 2.0 : 1.0) + 12.0 * inst[i].U;
   }
@@ -572,12 +737,18 @@ dialsort_status_t dialsort_batch_describe(dialsort_batch_t b, uint32_t index, di
   uint32_t p = 0;
   while (p < b->count && b->order[p] != index) ++p;
   const Req& r = b->h_reqs[p];
-  const uint32_t regime = r.mode == MODE_SMEM32 ? DIALSORT_REGIME_SMEM32
-                          : r.mode == MODE_SMEM16 ? DIALSORT_REGIME_SMEM16
-                                                  : DIALSORT_REGIME_GLOBAL_CRN;
-  *cfg = dialsort_hist_config_t{regime, 3u, 0u, kThreads, r.replicas, 1u};
-  if (items)
-    for (int k = 0; k < 4; ++k) items[k] = r.count[k];
+  const uint32_t regime = r.mode == MODE_SMEM32           ? DIALSORT_REGIME_SMEM32
+                          : r.mode == MODE_SMEM16         ? DIALSORT_REGIME_SMEM16
+                          : r.mode == MODE_TWO_LEVEL_ENG  ? DIALSORT_REGIME_TWO_LEVEL
+                                                          : DIALSORT_REGIME_GLOBAL_CRN;
+  const uint32_t crn_cfg = r.crn == CRN_ON ? 1u : r.crn == CRN_OFF ? 2u : 3u;
+  *cfg = dialsort_hist_config_t{regime, crn_cfg, 0u, kThreads, r.replicas, 1u, 0u};
+  if (items) {  // zero, histogram (two-level: partition + count), offsets, expand
+    items[0] = r.count[PH_ZERO - 1];
+    items[1] = r.count[PH_PART - 1] + r.count[PH_HIST - 1];
+    items[2] = r.count[PH_OFFS - 1];
+    items[3] = r.count[PH_EXPAND - 1];
+  }
   return DIALSORT_OK;
 }
 

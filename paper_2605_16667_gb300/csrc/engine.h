@@ -15,7 +15,29 @@ constexpr uint32_t kWindow = 256;        // requests examined per work search (o
 constexpr uint32_t kQuickCtas = 32;      // served mode: CTAs that watch the doorbell (fast pick-up)
 constexpr uint32_t kHistSmem = 48 * 1024;  // dynamic shared memory for shared-memory histogram items
 
-enum Phase : uint32_t { PH_FREE = 0, PH_ZERO = 1, PH_HIST = 2, PH_OFFS = 3, PH_EXPAND = 4, PH_DONE = 5 };
+// Two-level ingestion inside the engine (universes past the shared-memory
+// sub-histogram, up to 2^22 bins): bucket = key >> 14.  A partition item
+// groups the in-range keys of one 8192-key tile by bucket and writes their
+// low 14 bits (uint16) to the request's scratch, with one segment word per
+// (tile, bucket); a histogram item then counts one bucket's low parts over a
+// range of tiles in packed 16-bit shared-memory counters (32 KB) and adds
+// them into H.
+constexpr uint32_t kPartKeys = 8192;
+constexpr uint32_t kBucketBits = 14;
+constexpr uint32_t kMaxBuckets = 256;
+constexpr uint32_t MODE_TWO_LEVEL_ENG = 3;  // Req.mode beside hist_device.cuh's HistMode values
+
+// Phases in order; a request skips those with no items.
+enum Phase : uint32_t {
+  PH_FREE = 0,
+  PH_ZERO = 1,
+  PH_PART = 2,  // two-level only: partition tiles by bucket
+  PH_HIST = 3,
+  PH_OFFS = 4,
+  PH_EXPAND = 5,
+  PH_DONE = 6
+};
+constexpr uint32_t kPhases = 5;  // work phases PH_ZERO .. PH_EXPAND
 
 // Immutable description of one request (device memory).
 struct Req {
@@ -35,9 +57,12 @@ struct Req {
   uint32_t words_per_copy;
   uint32_t owned;     // the single histogram item stores every bin of H (H needs no zeroing)
   uint32_t out_aligned;
-  uint32_t count[4];  // items of the zero, histogram, offsets and expand phases
+  uint32_t count[kPhases];  // items of the zero, partition, histogram, offsets and expand phases
   uint32_t first_phase;
   uint32_t zero_H;    // the zero phase clears H[0..U) before clearing desc
+  uint32_t buckets;   // two-level: buckets of 2^kBucketBits bins
+  uint16_t* low;      // two-level: low parts, kPartKeys per partition tile
+  uint32_t* seg;      // two-level: per (tile, bucket) start | count << 16 within the tile
 };
 
 // Mutable progress of one request (device memory).  One 64-bit word holds
@@ -54,10 +79,11 @@ struct State {
   unsigned long long word;
   unsigned long long seq;       // admission order (smaller = older = served first)
   unsigned long long t_done;    // %globaltimer when the request finished
-  uint32_t done[4];             // items finished, per phase
+  uint32_t done[kPhases];       // items finished, per phase
   uint32_t err;                 // error bits of this request
-  uint32_t pad[5];
+  uint32_t pad[4];
 };
+static_assert(sizeof(State) == 64, "State is one 64-byte record");
 
 __host__ __device__ inline unsigned long long pack_word(uint64_t seq, uint32_t phase, uint32_t next) {
   return ((unsigned long long)(uint32_t)seq << 32) | ((unsigned long long)(phase & 0xffu) << 24) |
@@ -111,9 +137,11 @@ struct ReqPlanInput {
   uint64_t n;
   uint32_t U;
   uint32_t key_bytes;
+  uint32_t skew = 0;  // dialsort_skew_class_t, 0 = unknown
 };
 void plan_request(const ReqPlanInput& in, Req* r);
-// Bytes of reconstruction scratch (desc, O, first) the request needs, 256-aligned.
+// Bytes of scratch the request needs, 256-aligned: two-level ingestion (low
+// parts, segment words), then reconstruction (desc, O, first).
 size_t request_scratch_bytes(const Req& r);
 // Points desc / O / first into `base` (the request's scratch region).
 void place_request_scratch(Req* r, char* base);

@@ -111,9 +111,43 @@ cudaError_t launch_histogram(const void* keys, uint32_t key_bytes, uint64_t n, u
 //     warp with the CRN on); with H resident in L2 it needs no merge at all.
 constexpr uint32_t kGlobalHotBins = 8192;  // 32 KB: two 1024-thread CTAs per SM still fit
 
+namespace {
+dialsort_status_t plan_core(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
+                            const dialsort_hist_config_t& c, const DeviceInfo& dev, HistPlan* plan);
+}
+
 dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
-                                 const dialsort_hist_config_t* cfg, const DeviceInfo& dev, HistPlan* plan) {
-  dialsort_hist_config_t c = cfg ? *cfg : dialsort_hist_config_t{0, 0, 0, 0, 0, 0};
+                                 const dialsort_hist_config_t* cfg, const DeviceInfo& dev, HistPlan* plan,
+                                 bool use_table) {
+  dialsort_hist_config_t c = cfg ? *cfg : dialsort_hist_config_t{};
+  if (skew_hint > 3) return DIALSORT_ERR_INVALID_ARG;
+  const bool all_auto = c.regime == 0 && c.crn == 0 && c.blocks == 0 && c.threads == 0 && c.replicas == 0 &&
+                        c.cluster == 0;
+  dialsort_hist_config_t t;
+  uint32_t per_sm = 0;
+  if (use_table && all_auto && tuned_choice(n, U, key_bytes, skew_hint, &t, &per_sm)) {
+    // the measured entry; an entry that does not apply to this shape falls back to the cost model
+    const uint32_t sms = dev.sms > 0 ? (uint32_t)dev.sms : 152u;
+    if (per_sm) t.blocks = sms * per_sm;
+    if (t.regime == DIALSORT_REGIME_SMEM32 || t.regime == DIALSORT_REGIME_SMEM16) {
+      // never more CTAs than keep the end-of-kernel merge below about 1/8 of the keys
+      const uint64_t rep = t.replicas ? t.replicas : 1;
+      const uint64_t max_blocks = std::max<uint64_t>(1, n / (8ull * U * rep));
+      if (t.blocks > max_blocks) t.blocks = (uint32_t)max_blocks;
+    }
+    HistPlan p;
+    if (plan_core(n, U, key_bytes, skew_hint, t, dev, &p) == DIALSORT_OK) {
+      p.tuned = true;
+      *plan = p;
+      return DIALSORT_OK;
+    }
+  }
+  return plan_core(n, U, key_bytes, skew_hint, c, dev, plan);
+}
+
+namespace {
+dialsort_status_t plan_core(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
+                            const dialsort_hist_config_t& c, const DeviceInfo& dev, HistPlan* plan) {
   HistPlan p;
   const size_t smem_cap = dev.smem_optin ? dev.smem_optin : 227u * 1024u;
   const uint32_t sms = dev.sms > 0 ? (uint32_t)dev.sms : 152u;
@@ -142,7 +176,7 @@ dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uin
     else if (merge_cheap && u16_words * 4 <= smem_cap)
       regime = DIALSORT_REGIME_SMEM16;
     else
-      regime = skew_hint == 1 ? DIALSORT_REGIME_GLOBAL : DIALSORT_REGIME_GLOBAL_CRN;
+      regime = skew_hint == DIALSORT_SKEW_LOW ? DIALSORT_REGIME_GLOBAL : DIALSORT_REGIME_GLOBAL_CRN;
   }
   p.regime = regime;
   // config: 0 auto, 1 on, 2 off, 3 adaptive.  Auto: adaptive, except off for the plain GLOBAL
@@ -154,7 +188,7 @@ dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uin
   else if (c.crn == 3)
     p.crn = CRN_ADAPTIVE;
   else
-    p.crn = (regime == DIALSORT_REGIME_GLOBAL || skew_hint == 1) ? CRN_OFF : CRN_ADAPTIVE;
+    p.crn = (regime == DIALSORT_REGIME_GLOBAL || skew_hint == DIALSORT_SKEW_LOW) ? CRN_OFF : CRN_ADAPTIVE;
   p.threads = c.threads ? c.threads : 1024;
 
   if (regime == DIALSORT_REGIME_SMEM32 || regime == DIALSORT_REGIME_SMEM16) {
@@ -193,5 +227,6 @@ dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uin
   *plan = p;
   return DIALSORT_OK;
 }
+}  // namespace
 
 }  // namespace dialsort

@@ -42,12 +42,25 @@ struct HistPlan {
   uint32_t cluster = 1;
   uint32_t words_per_copy = 0;  // 32-bit words per shared-memory sub-histogram copy
   size_t smem_bytes = 0;        // dynamic shared memory per CTA
+  bool tuned = false;           // taken from the measured tuning table
 };
 
 // Fills every field of a plan (the autotuner); cfg fields that are non-zero
 // are taken as given.  Returns INVALID_ARG when a forced choice cannot work.
+// With use_table and an all-automatic cfg, the measured tuning table's entry
+// for (n, U, key_bytes, skew_hint) is tried first (plan->tuned says so).
 dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew_hint,
-                                 const dialsort_hist_config_t* cfg, const DeviceInfo& dev, HistPlan* plan);
+                                 const dialsort_hist_config_t* cfg, const DeviceInfo& dev, HistPlan* plan,
+                                 bool use_table = true);
+
+// The tuning table's entry nearest to (n, U) for this key width and skew
+// class, as launch choices (blocks left 0; blocks_per_sm separately, 0 =
+// automatic).  False when the table has nothing near.
+bool tuned_choice(uint64_t n, uint32_t U, uint32_t key_bytes, uint32_t skew, dialsort_hist_config_t* cfg,
+                  uint32_t* blocks_per_sm);
+// The skew class (dialsort_skew_class_t) of the probe's counts {samples,
+// equal neighbours, neighbour pairs, top multiplicity}.
+uint32_t skew_class_of(const uint32_t stats[4], uint32_t U);
 
 // Step 1 kernels (H must already be zero).  hist.cu
 // phi (optional): index = phi[key] for keys < M (see KeyMap); key_bytes 1, 2 or 4.

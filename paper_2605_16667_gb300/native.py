@@ -22,11 +22,17 @@ STATUS = ctypes.c_int
 
 class dialsort_hist_config_t(ctypes.Structure):
     _fields_ = [("regime", U32), ("crn", U32), ("blocks", U32), ("threads", U32), ("replicas", U32),
-                ("cluster", U32)]
+                ("cluster", U32), ("skew", U32)]
+
+
+class dialsort_skew_t(ctypes.Structure):
+    _fields_ = [("samples", U32), ("equal_neighbours", U32), ("neighbour_pairs", U32), ("top_multiplicity", U32),
+                ("skew_class", U32), ("reserved", U32)]
 
 
 class dialsort_instance_t(ctypes.Structure):
-    _fields_ = [("keys", P), ("H", P), ("out", P), ("n", U64), ("U", U32), ("key_bytes", U32)]
+    _fields_ = [("keys", P), ("H", P), ("out", P), ("n", U64), ("U", U32), ("key_bytes", U32), ("skew", U32),
+                ("reserved", U32)]
 
 
 class dialsort_server_cfg_t(ctypes.Structure):
@@ -34,7 +40,7 @@ class dialsort_server_cfg_t(ctypes.Structure):
 
 
 class dialsort_request_t(ctypes.Structure):
-    _fields_ = [("keys", P), ("n", U64), ("U", U32), ("key_bytes", U32), ("kind", U32), ("reserved", U32)]
+    _fields_ = [("keys", P), ("n", U64), ("U", U32), ("key_bytes", U32), ("kind", U32), ("skew", U32)]
 
 
 class dialsort_result_t(ctypes.Structure):
@@ -57,6 +63,10 @@ SIGNATURES = {
     "dialsort_histogram_u16": (STATUS, [P, U64, U32, P, P]),
     "dialsort_histogram_ex": (STATUS, [P, U32, U64, U32, P, P, P]),
     "dialsort_plan_histogram": (STATUS, [U64, U32, U32, U32, P]),
+    "dialsort_probe_skew": (STATUS, [P, U32, U64, U32, P, P]),
+    "dialsort_probe_skew_batched": (STATUS, [P, U32, P]),
+    "dialsort_tune_table_load": (STATUS, [ctypes.c_char_p]),
+    "dialsort_tune_table_size": (U32, []),
     "dialsort_histogram_workspace_size": (SZ, [U64, U32, U32]),
     "dialsort_histogram_ws": (STATUS, [P, U32, U64, U32, P, P, P, SZ, P]),
     "dialsort_reconstruct_workspace_size": (SZ, [U32, U64]),
@@ -66,6 +76,9 @@ SIGNATURES = {
     "dialsort_read_chunk_offsets": (STATUS, [P, U32, U64, P, P]),
     "dialsort_reconstruct_noalloc": (STATUS, [P, U32, P, U64, P]),
     "dialsort_histogram_accumulate": (STATUS, [P, U32, U64, U32, P, P, SZ, P]),
+    "dialsort_chunked_workspace_size": (SZ, [U64, U32, U32, U64, INT]),
+    "dialsort_histogram_chunked": (STATUS, [P, U32, U64, U32, U64, P, P, SZ, P, P]),
+    "dialsort_sort_chunked": (STATUS, [P, U32, U64, U32, U64, P, P, SZ, P, P]),
     "dialsort_sort_mapped_workspace_size": (SZ, [U64, U32]),
     "dialsort_sort_mapped": (STATUS, [P, U32, U64, P, U32, P, U32, P, P, SZ, P]),
     "dialsort_radix_workspace_size": (SZ, [U64]),
@@ -77,6 +90,7 @@ SIGNATURES = {
     "dialsort_sort_workspace_size": (SZ, [U64, U32]),
     "dialsort_sort": (STATUS, [P, U64, U32, P, P, SZ, P]),
     "dialsort_sort_u16": (STATUS, [P, U64, U32, P, P, SZ, P]),
+    "dialsort_sort_ex": (STATUS, [P, U32, U64, U32, P, P, P, SZ, P]),
     "dialsort_sort_histogram": (P, [P]),
     "dialsort_batch_create": (STATUS, [P, U32, INT, P]),
     "dialsort_batch_workspace_size": (SZ, [P]),

@@ -65,8 +65,18 @@ def test_host_validation_rejects_bad_arguments_before_launch(lib):
     assert lib.dialsort_reconstruct(4096, 16, 8192, 10, 4096, 1, None) == 8  # workspace too small
 
 
-def test_autotuner_plans_without_gpu():
+@pytest.fixture
+def cost_model():
+    """The planner without a measured table (the cost model alone); the default table afterwards."""
     import paper_2605_16667_gb300 as ds
+
+    ds.tune_table_load(None)
+    yield ds
+    ds.tune_table_load(ds.TUNE_TABLE if os.path.exists(ds.TUNE_TABLE) else None)
+
+
+def test_autotuner_plans_without_gpu(cost_model):
+    ds = cost_model
 
     p = ds.plan_histogram(1 << 28, 1 << 8)
     assert p["regime_name"] == "smem32" and p["blocks"] >= 1

@@ -89,7 +89,54 @@ def test_batch_relaunch_and_plan_description(ds):
         for i, (k, u) in enumerate(inst):
             np.testing.assert_array_equal(host(b.out[i], np.uint32), np.sort(k))
     regimes = {b.describe(i)["regime_name"] for i in range(len(inst))}
-    assert regimes <= {"smem32", "smem16", "global_crn"}
+    assert regimes <= {"smem32", "smem16", "global_crn", "two_level"}
+    b.close()
+
+
+TWO_LEVEL_CASES = [  # (n, U, dist, width, offset): universes past the packed sub-histogram, up to 2^22 bins
+    (13_000, 24_577, "uniform", 4, 0), (12_289, 24_577, "zipf", 4, 1), (40_000, 65536, "uniform", 2, 0),
+    (6 * 8192 + 5, 65536, "all_equal", 2, 3), (3 * 8192 + 5, 40000, "sorted", 4, 2),
+    ((1 << 20) + 77, 100003, "zipf", 4, 0), ((1 << 20) + 77, 1 << 20, "uniform", 4, 1),
+    (3 << 20, 3 * (1 << 20) + 1, "uniform", 4, 0), ((1 << 21) + 13, 1 << 22, "zipf", 4, 0),
+    ((1 << 21) + 13, 1 << 22, "all_equal", 4, 2), (5_000_003, 300_007, "runs", 4, 0),
+    (2_000_001, 1 << 21, "sorted", 4, 0), (40_000, 65535, "zipf_perm", 2, 1),
+]
+
+
+@pytest.mark.parametrize("sort", [True, False])
+def test_batch_two_level_instances(ds, sort):
+    inst = [(gen.keys(n, U, d, width=w, param=4096 if d == "runs" else None, stream=90 + i), U, o)
+            for i, (n, U, d, w, o) in enumerate(TWO_LEVEL_CASES)]
+    inst.append((gen.keys(300_000, 256, "uniform", stream=99), 256, 0))  # a small-universe neighbour
+    keys = [dev(k, o) for k, _, o in inst]
+    b = ds.Batch(keys, [u for _, u, _ in inst], sort=sort)
+    b.launch()
+    torch.cuda.synchronize()
+    assert ds.stream_status() == ds.OK
+    for i, (k, u, _) in enumerate(inst):
+        d = b.describe(i)
+        if i < len(TWO_LEVEL_CASES):
+            assert d["regime_name"] == "two_level", (i, d)
+            assert d["items"][1] >= (k.size + 8191) // 8192 + (u + 16383) // 16384  # partition + count items
+        H_ref, _ = oracle.histogram(k, u)
+        np.testing.assert_array_equal(host(b.H[i], np.uint32), H_ref, err_msg=f"instance {i} n={k.size} U={u}")
+        if sort:
+            np.testing.assert_array_equal(host(b.out[i], k.dtype), oracle.reconstruct(H_ref, u, width=k.dtype.itemsize),
+                                          err_msg=f"instance {i}")
+    b.close()
+
+
+def test_batch_two_level_reports_out_of_range_keys(ds):
+    k = gen.keys(100_000, 70_000, "uniform", stream=98)
+    bad = k.copy()
+    bad[12345] = 70_000
+    bad[99_999] = 0xFFFFFFFF
+    b = ds.Batch([dev(bad)], [70_000], sort=False)
+    assert b.describe(0)["regime_name"] == "two_level"
+    b.launch()
+    torch.cuda.synchronize()
+    assert ds.stream_status() == ds.ERR_KEY_RANGE
+    np.testing.assert_array_equal(host(b.H[0], np.uint32), oracle.histogram(bad, 70_000)[0])
     b.close()
 
 

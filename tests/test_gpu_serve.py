@@ -68,9 +68,10 @@ def test_results_in_the_mix_equal_results_alone(ds):
 
 
 def test_admission_waits_for_budget(ds):
-    # each request needs ~4 MB of H + 4 MB of output; a 10 MB budget admits one at a time
+    # each request needs ~4 MB of H + 4 MB of output + 2 MB of two-level scratch (16-bit low parts); a
+    # 12 MB budget admits one at a time
     keys = [dev(gen.keys(1 << 20, 1 << 20, "uniform", stream=95 + i)) for i in range(6)]
-    srv = ds.Server(hbm_budget_bytes=10 << 20, max_slots=8)
+    srv = ds.Server(hbm_budget_bytes=12 << 20, max_slots=8)
     ts = [srv.submit(k, 1 << 20, "sort") for k in keys]
     for t, k in zip(ts, keys):
         res = srv.wait(t)
