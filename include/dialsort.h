@@ -418,7 +418,9 @@ typedef struct {
   uint32_t U;
   uint32_t key_bytes;
   uint32_t skew;     /* dialsort_skew_class_t of the keys, 0 = unknown (dialsort_probe_skew_batched) */
-  uint32_t reserved; /* 0 */
+  uint32_t regime;   /* 0 = automatic; else the dialsort_regime_t step 1 must use (SMEM32, SMEM16,
+                        GLOBAL_CRN, GLOBAL, or TWO_LEVEL for U <= 2^22); one that cannot apply makes
+                        dialsort_batch_create return INVALID_ARG */
 } dialsort_instance_t;
 
 /*

@@ -437,7 +437,7 @@ class Batch:
     tensors (allocated when None); out: list of output tensors (allocated when sort and None).
     """
 
-    def __init__(self, keys, U, H=None, out=None, *, sort: bool = True, skew=None):
+    def __init__(self, keys, U, H=None, out=None, *, sort: bool = True, skew=None, regime=None):
         L = native.load()
         n = len(keys)
         self.keys = list(keys)
@@ -459,6 +459,9 @@ class Batch:
             arr[i].n = self.keys[i].numel()
             arr[i].U = self.U[i]
             arr[i].key_bytes = _width(self.keys[i])
+            if regime is not None:  # one name / number for all, or one per instance
+                r = regime if isinstance(regime, (str, int)) else regime[i]
+                arr[i].regime = REGIMES[r] if isinstance(r, str) else int(r)
             if skew is not None and skew != "probe":
                 arr[i].skew = SKEW_CLASSES[skew[i]] if isinstance(skew[i], str) else int(skew[i])
         if skew == "probe" and n:  # one probe launch for every instance

@@ -74,13 +74,18 @@ __host__ __device__ __forceinline__ uint64_t num_chunks_of(const Req& r) {
   return ((uint64_t)r.U + kChunkBins - 1) / kChunkBins;
 }
 
+// Offsets groups (look-back descriptors) of a sorting request; its offsets items take offs_per_item each.
+__host__ __device__ __forceinline__ uint64_t offs_groups_of(const Req& r) {
+  return r.count[PH_OFFS - 1] ? offset_groups(num_chunks_of(r)) : 0;
+}
+
 __device__ __forceinline__ uint32_t next_phase(const Req& r, uint32_t ph) {
   for (uint32_t p = ph + 1; p <= PH_EXPAND; ++p)
     if (r.count[p - 1]) return p;
   return PH_DONE;
 }
 
-// The zero phase clears, in kZeroWords-word items, the concatenation of H
+// The zero phase clears, in zero_words_item-word items, the concatenation of H
 // (when the histogram phase adds into it) and the look-back descriptors of
 // the offsets phase.  Doing this on the device keeps admission free of
 // kernels (a memset could not start while the engine occupies every SM).
@@ -96,9 +101,9 @@ __device__ void zero_words(uint32_t* p, uint64_t w0, uint64_t w1) {  // p 16-byt
 
 __device__ void zero_item(const Req& r, uint32_t item) {
   const uint64_t h_words = r.zero_H ? (uint64_t)r.U : 0;
-  const uint64_t d_words = r.desc ? 2ull * r.count[PH_OFFS - 1] : 0;  // one descriptor per offsets group
-  const uint64_t w0 = (uint64_t)item * kZeroWords;
-  const uint64_t w1 = min(w0 + kZeroWords, h_words + d_words);
+  const uint64_t d_words = r.desc ? 2ull * offs_groups_of(r) : 0;  // one descriptor per offsets group
+  const uint64_t w0 = (uint64_t)item * r.zero_words_item;
+  const uint64_t w1 = min(w0 + r.zero_words_item, h_words + d_words);
   if (w0 < h_words) zero_words(r.H, w0, min(w1, h_words));
   if (w1 > h_words) zero_words(reinterpret_cast<uint32_t*>(r.desc), max(w0, h_words) - h_words, w1 - h_words);
 }
@@ -259,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   uint64_t idle_since = 0;  // thread 0 only
   uint32_t backoff = 500;   // ns; doubles while idle (every thread keeps the same value)
+  uint32_t round = 0;       // work searches so far (scrambles the batched-mode choice)
   unsigned long long seen_bell = 0;  // thread 0 only: the doorbell value at the last ring scan
 
   for (;;) {
@@ -266,6 +272,7 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
     // first barrier makes sure every thread has read last round's shared words
     // before thread 0 rewrites them.
     __syncthreads();
+    ++round;
     if (tid == 0) {
       s_base = L.served ? 0u : ld_volatile_u32(&L.ctl->tail);
       s_cmd = CMD_SLEEP;
@@ -282,7 +289,15 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
         const uint32_t ph = word_phase(w);
         done = (ph == PH_DONE);
         if (ph >= PH_ZERO && ph <= PH_EXPAND && word_next(w) < ld_volatile_u32(&L.reqs[slot].count[ph - 1]))
-          key = ((uint64_t)word_seq(w) << 8) | tid;
+        {
+          // An order scrambled per CTA and per round, so that hundreds of CTAs spread over the
+          // requests with work instead of all contending for one request's next item (one claim per
+          // round).  Batched: any request of the window.  Served: among the oldest cohort of 32
+          // admissions with work (older cohorts first keeps the tail latency).
+          const uint64_t mix = (uint32_t)(((tid + 1u) * 0x9E3779B1u) ^ (blockIdx.x * 0x85EBCA6Bu) ^
+                                          (round * 0xC2B2AE35u)) >> 8;
+          key = L.served ? (((uint64_t)(word_seq(w) >> 5) << 32) | (mix << 8) | tid) : ((mix << 8) | tid);
+        }
       }
       const uint32_t notdone = __ballot_sync(0xffffffffu, !done);
 #pragma unroll
@@ -398,18 +413,34 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
         else
           run_hist(r, item, reinterpret_cast<uint32_t*>(dyn), L.err, st);
         break;
-      case PH_OFFS:
-        offsets_group(r.H, r.U, r.n, num_chunks_of(r), item, r.desc, r.O, r.first, L.err,
-                      *reinterpret_cast<OffsetsSmem*>(dyn));
+      case PH_OFFS: {  // offs_per_item consecutive groups, in order (a group looks back only at earlier ones)
+        const uint64_t g1 = min((uint64_t)(item + 1) * r.offs_per_item, offs_groups_of(r));
+        for (uint64_t g = (uint64_t)item * r.offs_per_item; g < g1; ++g)
+          offsets_group(r.H, r.U, r.n, num_chunks_of(r), g, r.desc, r.O, r.first, L.err,
+                        *reinterpret_cast<OffsetsSmem*>(dyn));
         break;
-      default:
-        if (r.key_bytes == 4)
-          expand_tile<uint32_t>(r.H, r.U, r.n, num_chunks_of(r), r.O, r.first, static_cast<uint32_t*>(r.out),
-                                r.out_aligned, item, *reinterpret_cast<ExpandSmem*>(dyn));
-        else
-          expand_tile<uint16_t>(r.H, r.U, r.n, num_chunks_of(r), r.O, r.first, static_cast<uint16_t*>(r.out),
-                                r.out_aligned, item, *reinterpret_cast<ExpandSmem*>(dyn));
+      }
+      default: {  // expand_per_item output tiles (or chunk groups of a sparse H) per item
+        const uint64_t units = r.by_bins ? offset_groups(num_chunks_of(r)) : (r.n + kTileKeys - 1) / kTileKeys;
+        const uint64_t u1 = min((uint64_t)(item + 1) * r.expand_per_item, units);
+        for (uint64_t u = (uint64_t)item * r.expand_per_item; u < u1; ++u) {
+          if (r.by_bins) {
+            if (r.key_bytes == 4)
+              expand_bins<uint32_t>(r.H, r.U, r.n, num_chunks_of(r), r.O, static_cast<uint32_t*>(r.out), u);
+            else
+              expand_bins<uint16_t>(r.H, r.U, r.n, num_chunks_of(r), r.O, static_cast<uint16_t*>(r.out), u);
+          } else {
+            if (r.key_bytes == 4)
+              expand_tile<uint32_t>(r.H, r.U, r.n, num_chunks_of(r), r.O, r.first, static_cast<uint32_t*>(r.out),
+                                    r.out_aligned, u, *reinterpret_cast<ExpandSmem*>(dyn));
+            else
+              expand_tile<uint16_t>(r.H, r.U, r.n, num_chunks_of(r), r.O, r.first, static_cast<uint16_t*>(r.out),
+                                    r.out_aligned, u, *reinterpret_cast<ExpandSmem*>(dyn));
+            __syncthreads();  // the tile's shared buffers are reused by the next
+          }
+        }
         break;
+      }
     }
 
     // ---- report; the last item of a phase publishes the next phase
@@ -441,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 4) engine_kernel(Launch L) {
 
 // ---------------------------------------------------------------- host side
 
-void plan_request(const ReqPlanInput& in, Req* r) {
+bool plan_request(const ReqPlanInput& in, Req* r) {
   std::memset(r, 0, sizeof(Req));
   r->keys = in.keys;
   r->H = in.H;
@@ -449,41 +480,60 @@ void plan_request(const ReqPlanInput& in, Req* r) {
   r->n = in.n;
   r->U = in.U;
   r->key_bytes = in.key_bytes;
-  // the CRN by skew class: the tuning table's measured choice for this shape and class where it has
-  // one; else off when equal keys rarely meet, on for runs, adaptive per warp otherwise
-  r->crn = CRN_ADAPTIVE;
-  dialsort_hist_config_t t;
-  uint32_t per_sm = 0;
-  if (in.skew != DIALSORT_SKEW_UNKNOWN && tuned_choice(in.n, in.U, in.key_bytes, in.skew, &t, &per_sm) && t.crn)
-    r->crn = t.crn == 1 ? CRN_ON : t.crn == 2 ? CRN_OFF : CRN_ADAPTIVE;
-  else if (in.skew == DIALSORT_SKEW_LOW)
-    r->crn = CRN_OFF;
-  else if (in.skew == DIALSORT_SKEW_RUNS)
-    r->crn = CRN_ON;
+  // the CRN by skew class: off when equal keys rarely meet, on for runs, adaptive per warp otherwise
+  // (the tuning table's CRN choices were measured on the single-instance kernels, whose CTA shapes and
+  // shared-memory hot prefix differ, so they are not carried over)
+  r->crn = in.skew == DIALSORT_SKEW_LOW ? CRN_OFF : in.skew == DIALSORT_SKEW_RUNS ? CRN_ON : CRN_ADAPTIVE;
   const uint64_t cap32 = kHistSmem / 4, cap16 = 2 * (kHistSmem / 4);
   const uint64_t U = in.U, n = in.n;
-  // two-level: past the packed sub-histogram, up to 2^22 bins, with enough keys that one pass of
-  // partition + count beats one L2 atomic per key (the B x 2^13-word merges cost about U / 2 adds)
-  const bool two_level = U > cap16 && U <= ((uint64_t)kMaxBuckets << kBucketBits) && 2 * n >= U;
-  if (two_level) {
-    r->mode = MODE_TWO_LEVEL_ENG;
+  const bool fits32 = align_up(U, 4) <= cap32, fits16 = align_up((U + 1) / 2, 4) <= cap16 / 2;
+  const bool fits_tl = U <= ((uint64_t)kMaxBuckets << kBucketBits);
+  uint32_t mode;
+  switch (in.regime) {
+    case DIALSORT_REGIME_AUTO:
+      // (the two-level form is taken only when forced: measured inside the engine on instances of up
+      // to 2^24 keys, whose H stays in L2, one L2 atomic per key was faster at every (n, U) tried)
+      if (n >= 2 * U && fits32)
+        mode = MODE_SMEM32;
+      else if (n >= 2 * U && fits16)
+        mode = MODE_SMEM16;
+      else
+        mode = MODE_GLOBAL;
+      break;
+    case DIALSORT_REGIME_SMEM32:
+      if (!fits32) return false;
+      mode = MODE_SMEM32;
+      break;
+    case DIALSORT_REGIME_SMEM16:
+      if (!fits16) return false;
+      mode = MODE_SMEM16;
+      break;
+    case DIALSORT_REGIME_GLOBAL_CRN:
+    case DIALSORT_REGIME_GLOBAL:
+      mode = MODE_GLOBAL;
+      if (in.regime == DIALSORT_REGIME_GLOBAL) r->crn = CRN_OFF;
+      break;
+    case DIALSORT_REGIME_TWO_LEVEL:
+      if (!fits_tl) return false;
+      mode = MODE_TWO_LEVEL_ENG;
+      break;
+    default:
+      return false;
+  }
+  r->mode = mode;
+  r->replicas = 1;
+  if (mode == MODE_TWO_LEVEL_ENG) {
     r->buckets = (uint32_t)((U + (1u << kBucketBits) - 1) >> kBucketBits);
     r->words_per_copy = (1u << kBucketBits) / 2u;
-    r->replicas = 1;
-  } else if (n >= 2 * U && align_up(U, 4) <= cap32) {
-    r->mode = MODE_SMEM32;
+  } else if (mode == MODE_SMEM32) {
     r->words_per_copy = (uint32_t)align_up(U, 4);
     uint32_t rep = 1;
     while (rep < 8 && (uint64_t)r->words_per_copy * 4 * rep * 2 <= kHistSmem) rep *= 2;
     r->replicas = rep;
-  } else if (n >= 2 * U && align_up((U + 1) / 2, 4) <= cap16 / 2) {
-    r->mode = MODE_SMEM16;
+  } else if (mode == MODE_SMEM16) {
     r->words_per_copy = (uint32_t)align_up((U + 1) / 2, 4);
-    r->replicas = 1;
   } else {
-    r->mode = MODE_GLOBAL;
     r->words_per_copy = (uint32_t)std::min<uint64_t>(align_up(U, 4), kHistSmem / 4);  // shared hot prefix
-    r->replicas = 1;
   }
   uint32_t n_hist;
   if (r->mode == MODE_TWO_LEVEL_ENG) {
@@ -497,19 +547,28 @@ void plan_request(const ReqPlanInput& in, Req* r) {
     n_hist = (uint32_t)(groups * r->buckets);
   } else {
     if (r->mode == MODE_GLOBAL)
-      r->item_keys = 65536;
+      r->item_keys = 65536ull * (in.served ? 1u : kBatchedHistScale);
     else
-      r->item_keys = align_up(std::max<uint64_t>(32768, 8ull * U * r->replicas), 8192);
+      r->item_keys = align_up(std::max<uint64_t>(32768ull * (in.served ? 1u : kBatchedHistScale),
+                                                 8ull * U * r->replicas), 8192);
     n_hist = (uint32_t)((n + r->item_keys - 1) / r->item_keys);
   }
   r->owned = (r->mode == MODE_SMEM32 && n_hist == 1) ? 1u : 0u;
   r->zero_H = r->owned ? 0u : 1u;
   r->count[PH_HIST - 1] = n_hist;
   const bool sort = in.out != nullptr && n > 0;
-  r->count[PH_OFFS - 1] = sort ? (uint32_t)offset_groups((U + kChunkBins - 1) / kChunkBins) : 0u;
-  r->count[PH_EXPAND - 1] = sort ? (uint32_t)((n + kTileKeys - 1) / kTileKeys) : 0u;
-  const uint64_t zero_words = (r->zero_H ? U : 0) + 2ull * r->count[PH_OFFS - 1];
-  r->count[PH_ZERO - 1] = (uint32_t)((zero_words + kZeroWords - 1) / kZeroWords);
+  const uint32_t groups = sort ? (uint32_t)offset_groups((U + kChunkBins - 1) / kChunkBins) : 0u;
+  r->zero_words_item = kZeroWords * (in.served ? 1u : kBatchedZeroScale);
+  r->offs_per_item = in.served ? 1u : kBatchedOffsPerItem;
+  r->expand_per_item = in.served ? 1u : kBatchedExpandPerItem;
+  r->count[PH_OFFS - 1] = (groups + r->offs_per_item - 1) / r->offs_per_item;
+  // a sparse H (fewer keys than bins / 4): each offsets group of chunks writes its own bins' runs, so the
+  // Theta(U) walk is spread over U / 8192 items instead of the few output tiles
+  r->by_bins = (sort && 4 * n < U) ? 1u : 0u;
+  const uint64_t units = r->by_bins ? groups : (n + kTileKeys - 1) / kTileKeys;
+  r->count[PH_EXPAND - 1] = !sort ? 0u : (uint32_t)((units + r->expand_per_item - 1) / r->expand_per_item);
+  const uint64_t zero_words = (r->zero_H ? U : 0) + 2ull * groups;
+  r->count[PH_ZERO - 1] = (uint32_t)((zero_words + r->zero_words_item - 1) / r->zero_words_item);
   r->out_aligned = (reinterpret_cast<uintptr_t>(in.out) & 15u) == 0;
   r->first_phase = PH_DONE;
   for (uint32_t p = PH_ZERO; p <= PH_EXPAND; ++p)
@@ -517,6 +576,7 @@ void plan_request(const ReqPlanInput& in, Req* r) {
       r->first_phase = p;
       break;
     }
+  return true;
 }
 
 // scratch of a sorting request: look-back descriptors (one per offsets group),
@@ -530,7 +590,7 @@ size_t two_level_scratch_bytes(const Req& r) {
 }  // namespace
 
 size_t request_scratch_bytes(const Req& r) {
-  const uint64_t groups = r.count[PH_OFFS - 1], tiles = r.count[PH_EXPAND - 1];
+  const uint64_t groups = offs_groups_of(r), tiles = (r.n + kTileKeys - 1) / kTileKeys;
   const size_t tl = two_level_scratch_bytes(r);
   if (groups == 0) return tl;
   const uint64_t chunks = num_chunks_of(r);
@@ -547,7 +607,7 @@ void place_request_scratch(Req* r, char* base) {
     r->seg = reinterpret_cast<uint32_t*>(base + align_up(tiles * kPartKeys * 2, 256));
     base += two_level_scratch_bytes(*r);
   }
-  const uint64_t groups = r->count[PH_OFFS - 1];
+  const uint64_t groups = offs_groups_of(*r);
   if (groups == 0) {
     r->desc = nullptr;
     r->O = nullptr;
@@ -664,8 +724,11 @@ dialsort_status_t dialsort_batch_create(const dialsort_instance_t* inst, uint32_
   std::vector<double> cost(count);
   for (uint32_t i = 0; i < count; ++i) {
     ReqPlanInput in{inst[i].keys, inst[i].H,  sort ? inst[i].out : nullptr, inst[i].n,
-                    inst[i].U,    inst[i].key_bytes, inst[i].skew <= 3 ? inst[i].skew : 0u};
-    plan_request(in, &plans[i]);
+                    inst[i].U,    inst[i].key_bytes, inst[i].skew <= 3 ? inst[i].skew : 0u, inst[i].regime};
+    if (!plan_request(in, &plans[i])) {
+      free_batch(b);
+      return DIALSORT_ERR_INVALID_ARG;
+    }
     cost[i] = (double)inst[i].n * inst[i].key_bytes * (sort ? 2.0 : 1.0) + 12.0 * inst[i].U;
   }
   b->order.resize(count);

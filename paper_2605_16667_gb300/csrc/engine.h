@@ -10,10 +10,17 @@ namespace dialsort {
 namespace eng {
 
 constexpr uint32_t kThreads = 256;       // worker CTA size (the step-2 routines assume 256)
-constexpr uint32_t kZeroWords = 16384;   // H words zeroed per zero item (64 KB)
+constexpr uint32_t kZeroWords = 16384;   // H words zeroed per zero item (64 KB; batched: x kBatchedZeroScale)
 constexpr uint32_t kWindow = 256;        // requests examined per work search (one per thread)
 constexpr uint32_t kQuickCtas = 32;      // served mode: CTAs that watch the doorbell (fast pick-up)
 constexpr uint32_t kHistSmem = 48 * 1024;  // dynamic shared memory for shared-memory histogram items
+// Batched mode: a claim costs a few microseconds of L2 round trips, so its items carry more work (the
+// zero phase's words, the offsets groups, the output tiles (or sparse chunk groups) and the histogram's
+// keys, times these factors).  Served mode keeps small items: one request then spreads over every CTA.
+constexpr uint32_t kBatchedZeroScale = 4;
+constexpr uint32_t kBatchedOffsPerItem = 4;
+constexpr uint32_t kBatchedExpandPerItem = 8;
+constexpr uint32_t kBatchedHistScale = 4;
 
 // Two-level ingestion inside the engine (universes past the shared-memory
 // sub-histogram, up to 2^22 bins): bucket = key >> 14.  A partition item
@@ -61,6 +68,10 @@ struct Req {
   uint32_t first_phase;
   uint32_t zero_H;    // the zero phase clears H[0..U) before clearing desc
   uint32_t buckets;   // two-level: buckets of 2^kBucketBits bins
+  uint32_t by_bins;   // the expand phase is bin-parallel (expand_bins: a sparse H), over the offsets groups
+  uint32_t zero_words_item;  // H / descriptor words per zero item
+  uint32_t offs_per_item;    // offsets groups per offsets item
+  uint32_t expand_per_item;  // output tiles (or sparse chunk groups) per expand item
   uint16_t* low;      // two-level: low parts, kPartKeys per partition tile
   uint32_t* seg;      // two-level: per (tile, bucket) start | count << 16 within the tile
 };
@@ -137,9 +148,12 @@ struct ReqPlanInput {
   uint64_t n;
   uint32_t U;
   uint32_t key_bytes;
-  uint32_t skew = 0;  // dialsort_skew_class_t, 0 = unknown
+  uint32_t skew = 0;    // dialsort_skew_class_t, 0 = unknown
+  uint32_t regime = 0;  // dialsort_regime_t to force, 0 = automatic
+  bool served = false;  // served mode: small items (latency); batched: larger items (throughput)
 };
-void plan_request(const ReqPlanInput& in, Req* r);
+// False when a forced regime cannot apply to the request.
+bool plan_request(const ReqPlanInput& in, Req* r);
 // Bytes of scratch the request needs, 256-aligned: two-level ingestion (low
 // parts, segment words), then reconstruction (desc, O, first).
 size_t request_scratch_bytes(const Req& r);

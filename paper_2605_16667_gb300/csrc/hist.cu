@@ -125,7 +125,8 @@ dialsort_status_t plan_histogram(uint64_t n, uint32_t U, uint32_t key_bytes, uin
                         c.cluster == 0;
   dialsort_hist_config_t t;
   uint32_t per_sm = 0;
-  if (use_table && all_auto && tuned_choice(n, U, key_bytes, skew_hint, &t, &per_sm)) {
+  // (an entry with regime 0 says the cost model is right at that shape: the untuned path below)
+  if (use_table && all_auto && tuned_choice(n, U, key_bytes, skew_hint, &t, &per_sm) && t.regime != 0) {
     // the measured entry; an entry that does not apply to this shape falls back to the cost model
     const uint32_t sms = dev.sms > 0 ? (uint32_t)dev.sms : 152u;
     if (per_sm) t.blocks = sms * per_sm;

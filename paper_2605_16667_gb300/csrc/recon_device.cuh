@@ -146,6 +146,74 @@ __host__ __device__ inline uint64_t offset_groups(uint64_t num_chunks) {
   return (num_chunks + kReconThreads / 32 - 1) / (kReconThreads / 32);
 }
 
+// Bin-parallel projection for a sparse histogram (n well below U, where an
+// output tile spans many chunks and one CTA would walk them all): item g
+// takes chunks [8 g, 8 g + 8), one per warp, and every bin k writes its own
+// run [start_k, start_k + H[k]) of Eq. (2) -- start_k from the chunk's offset
+// O[c] and a warp scan of the chunk's bins.  A lane writes runs of up to four
+// keys itself; longer runs are painted by the whole warp.  Positions at or
+// past n_cap are not written (sum(H) > n_cap is reported by the offsets).
+template <typename OutT>
+__device__ __forceinline__ void expand_bins(const uint32_t* __restrict__ H, uint32_t U, uint64_t n_cap,
+                                            uint64_t num_chunks, const uint64_t* __restrict__ O,
+                                            OutT* __restrict__ out, uint64_t g,
+                                            const OutT* __restrict__ inv = nullptr) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint64_t c = g * (kReconThreads / 32) + warp;
+  if (c >= num_chunks) return;
+  uint64_t run = O[c];
+  if (O[c + 1] == run || run >= n_cap) return;  // an empty chunk, or one past the output (warp-uniform)
+#pragma unroll 1
+  for (uint32_t r = 0; r < kChunkBins / 128; ++r) {
+    uint32_t h[4];
+    const uint64_t b0 = c * kChunkBins + r * 128 + lane * 4ull;
+    load_bins4(H, b0, U, h);
+    const uint32_t t4 = h[0] + h[1] + h[2] + h[3];
+    uint32_t x = t4;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= (uint32_t)d) x += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+    if (total == 0) continue;  // warp-uniform
+    const uint64_t s0 = run + (x - t4);
+    uint64_t st = s0;
+    uint32_t longmask = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (h[j] != 0 && h[j] <= 4) {
+        const OutT key = inv != nullptr ? inv[b0 + j] : (OutT)(b0 + j);
+        for (uint32_t q = 0; q < h[j]; ++q)
+          if (st + q < n_cap) out[st + q] = key;
+      } else if (h[j] > 4) {
+        longmask |= 1u << j;
+      }
+      st += h[j];
+    }
+    uint32_t lanes = __ballot_sync(0xffffffffu, longmask != 0);
+    while (lanes) {  // long runs: the warp paints them one by one
+      const uint32_t src = (uint32_t)(__ffs(lanes) - 1);
+      lanes &= lanes - 1;
+      const uint32_t lm = __shfl_sync(0xffffffffu, longmask, src);
+      uint64_t ss = __shfl_sync(0xffffffffu, s0, src);
+      const uint64_t sb = c * kChunkBins + r * 128 + src * 4ull;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t hj = __shfl_sync(0xffffffffu, h[j], src);
+        if ((lm >> j) & 1u) {
+          const OutT key = inv != nullptr ? inv[sb + j] : (OutT)(sb + j);
+          for (uint32_t q = lane; q < hj; q += 32)
+            if (ss + q < n_cap) out[ss + q] = key;
+        }
+        ss += hj;
+      }
+    }
+    run += total;
+    if (run >= n_cap) return;  // warp-uniform
+  }
+}
+
 // Tiles crossed by at most this many short runs are painted run by run; others fill forward.
 // Runs of kLongRun slots or more (at most four per tile) are painted by the whole CTA.
 constexpr uint32_t kPaintRuns = 256;

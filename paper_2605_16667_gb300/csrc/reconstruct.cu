@@ -84,11 +84,12 @@ __global__ void __launch_bounds__(kReconThreads) project_kernel(const uint32_t* 
                                                                 uint64_t* desc, uint64_t* O, uint32_t* first_chunk,
                                                                 OutT* __restrict__ out, int out_aligned,
                                                                 const OutT* __restrict__ inv, uint32_t* err,
-                                                                int phase_mask) {
+                                                                int phase_mask, int by_bins) {
   __shared__ __align__(16) ProjSmem sm;
   const uint32_t tid = threadIdx.x;
   const uint64_t groups = offset_groups(num_chunks);
-  const uint64_t tiles = (phase_mask & 2) ? (n_cap + kTileKeys - 1) / kTileKeys : 0;
+  // expansion items: output tiles, or (a sparse H, by_bins) the offsets' chunk groups again
+  const uint64_t tiles = !(phase_mask & 2) ? 0 : by_bins ? groups : (n_cap + kTileKeys - 1) / kTileKeys;
   bool waited = false;
   for (;;) {
     if (tid == 0) sm.k = atomicAdd(&ctl->ticket, 1u);
@@ -118,7 +119,10 @@ __global__ void __launch_bounds__(kReconThreads) project_kernel(const uint32_t* 
       __syncthreads();
       waited = true;
     }
-    expand_tile<OutT>(H, U, n_cap, num_chunks, O, first_chunk, out, out_aligned, k - groups, sm.ex, inv);
+    if (by_bins)
+      expand_bins<OutT>(H, U, n_cap, num_chunks, O, out, k - groups, inv);
+    else
+      expand_tile<OutT>(H, U, n_cap, num_chunks, O, first_chunk, out, out_aligned, k - groups, sm.ex, inv);
   }
 }
 
@@ -217,7 +221,10 @@ cudaError_t launch_projection(const uint32_t* H, uint32_t U, uint64_t n, void* o
   int per_sm = 0;
   e = kernel_config(fn, kReconThreads, 0, true, &per_sm);
   if (e != cudaSuccess) return e;
-  const uint64_t work = offset_groups(L.num_chunks) + (phase_mask & 2 ? L.num_tiles : 0);
+  // a sparse H (fewer keys than bins / 4): bin-parallel expansion over the chunk groups
+  const int by_bins = 4 * n < (uint64_t)U ? 1 : 0;
+  const uint64_t work = offset_groups(L.num_chunks) +
+                        (phase_mask & 2 ? (by_bins ? offset_groups(L.num_chunks) : L.num_tiles) : 0);
   const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)dev.sms * std::max(per_sm, 1), std::max<uint64_t>(work, 1));
   ProjCtl* ctl = reinterpret_cast<ProjCtl*>(base + L.off_ticket);  // in the zeroed region
   uint64_t* desc = reinterpret_cast<uint64_t*>(base + L.off_desc);
@@ -227,15 +234,18 @@ cudaError_t launch_projection(const uint32_t* H, uint32_t U, uint64_t n, void* o
   if (out_bytes == 4)
     project_kernel<uint32_t><<<grid, kReconThreads, 0, stream>>>(H, U, n, L.num_chunks, ctl, desc, O, first,
                                                                  static_cast<uint32_t*>(out), aligned,
-                                                                 static_cast<const uint32_t*>(inv), err, phase_mask);
+                                                                 static_cast<const uint32_t*>(inv), err, phase_mask,
+                                                                 by_bins);
   else if (out_bytes == 2)
     project_kernel<uint16_t><<<grid, kReconThreads, 0, stream>>>(H, U, n, L.num_chunks, ctl, desc, O, first,
                                                                  static_cast<uint16_t*>(out), aligned,
-                                                                 static_cast<const uint16_t*>(inv), err, phase_mask);
+                                                                 static_cast<const uint16_t*>(inv), err, phase_mask,
+                                                                 by_bins);
   else
     project_kernel<uint8_t><<<grid, kReconThreads, 0, stream>>>(H, U, n, L.num_chunks, ctl, desc, O, first,
                                                                 static_cast<uint8_t*>(out), aligned,
-                                                                static_cast<const uint8_t*>(inv), err, phase_mask);
+                                                                static_cast<const uint8_t*>(inv), err, phase_mask,
+                                                                by_bins);
   return cudaGetLastError();
 }
 

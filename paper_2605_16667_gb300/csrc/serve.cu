@@ -147,8 +147,8 @@ struct dialsort_server_s {
 
   size_t block_bytes(const dialsort_request_t& r, Req* plan) const {
     ReqPlanInput in{r.keys, reinterpret_cast<uint32_t*>(256), r.kind ? reinterpret_cast<void*>(256) : nullptr, r.n,
-                    r.U, r.key_bytes, r.skew <= 3 ? r.skew : 0u};
-    plan_request(in, plan);
+                    r.U, r.key_bytes, r.skew <= 3 ? r.skew : 0u, 0u, true};
+    (void)plan_request(in, plan);  // automatic: always applies
     size_t b = align_up((size_t)r.U * 4, 256);
     if (r.kind) b += align_up((size_t)r.n * r.key_bytes, 256);
     return b + request_scratch_bytes(*plan);
@@ -168,9 +168,10 @@ struct dialsort_server_s {
       t.out = p;
       p += align_up((size_t)t.req.n * t.req.key_bytes, 256);
     }
-    ReqPlanInput in{t.req.keys, t.H, t.out, t.req.n, t.req.U, t.req.key_bytes, t.req.skew <= 3 ? t.req.skew : 0u};
+    ReqPlanInput in{t.req.keys, t.H, t.out, t.req.n, t.req.U, t.req.key_bytes, t.req.skew <= 3 ? t.req.skew : 0u,
+                    0u, true};
     Req& r = h_req_stage[s];
-    plan_request(in, &r);
+    (void)plan_request(in, &r);
     place_request_scratch(&r, p);
     const uint64_t seq = next_seq++;
     State& st = h_state_stage[s];

@@ -32,7 +32,7 @@ class dialsort_skew_t(ctypes.Structure):
 
 class dialsort_instance_t(ctypes.Structure):
     _fields_ = [("keys", P), ("H", P), ("out", P), ("n", U64), ("U", U32), ("key_bytes", U32), ("skew", U32),
-                ("reserved", U32)]
+                ("regime", U32)]
 
 
 class dialsort_server_cfg_t(ctypes.Structure):

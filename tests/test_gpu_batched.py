@@ -109,7 +109,8 @@ def test_batch_two_level_instances(ds, sort):
             for i, (n, U, d, w, o) in enumerate(TWO_LEVEL_CASES)]
     inst.append((gen.keys(300_000, 256, "uniform", stream=99), 256, 0))  # a small-universe neighbour
     keys = [dev(k, o) for k, _, o in inst]
-    b = ds.Batch(keys, [u for _, u, _ in inst], sort=sort)
+    regimes = ["two_level"] * len(TWO_LEVEL_CASES) + ["auto"]
+    b = ds.Batch(keys, [u for _, u, _ in inst], sort=sort, regime=regimes)
     b.launch()
     torch.cuda.synchronize()
     assert ds.stream_status() == ds.OK
@@ -131,13 +132,31 @@ def test_batch_two_level_reports_out_of_range_keys(ds):
     bad = k.copy()
     bad[12345] = 70_000
     bad[99_999] = 0xFFFFFFFF
-    b = ds.Batch([dev(bad)], [70_000], sort=False)
+    b = ds.Batch([dev(bad)], [70_000], sort=False, regime="two_level")
     assert b.describe(0)["regime_name"] == "two_level"
     b.launch()
     torch.cuda.synchronize()
     assert ds.stream_status() == ds.ERR_KEY_RANGE
     np.testing.assert_array_equal(host(b.H[0], np.uint32), oracle.histogram(bad, 70_000)[0])
     b.close()
+
+
+def test_batch_forced_regimes_and_refusals(ds):
+    k = gen.keys(200_000, 5000, "zipf", stream=97)
+    H_ref, _ = oracle.histogram(k, 5000)
+    for regime in ("smem32", "smem16", "global_crn", "global", "two_level"):
+        b = ds.Batch([dev(k)], [5000], sort=True, regime=regime)
+        assert b.describe(0)["regime_name"] == ("global_crn" if regime == "global" else regime)
+        b.launch()
+        torch.cuda.synchronize()
+        assert ds.stream_status() == ds.OK
+        np.testing.assert_array_equal(host(b.H[0], np.uint32), H_ref)
+        np.testing.assert_array_equal(host(b.out[0], np.uint32), oracle.reconstruct(H_ref, 5000))
+        b.close()
+    big = dev(gen.keys(1000, 1 << 23, "uniform", stream=96))
+    for regime in ("smem32", "smem16", "two_level", "cluster"):  # too large for these, or not built
+        with pytest.raises(ds.DialSortError):
+            ds.Batch([big], [1 << 23], sort=True, regime=regime)
 
 
 def test_batch_captured_in_a_cuda_graph(ds):

@@ -209,6 +209,32 @@ def test_reconstruct_matches_oracle(ds, U, dist, n):
     np.testing.assert_array_equal(host(out), oracle.reconstruct(H, U))
 
 
+@pytest.mark.parametrize("U,width", [(1 << 22, 4), ((1 << 20) + 9, 4), (65536, 2), (3 * 1024 + 5, 4)])
+@pytest.mark.parametrize("cap_kind", ["exact", "larger", "smaller"])
+def test_sparse_projection_short_and_long_runs(ds, U, width, cap_kind):
+    # fewer keys than bins / 4: the bin-parallel projection; bins holding 1-4 keys (a lane writes them),
+    # 5-300 keys and one bin of many keys (the warp paints them), spread over the universe
+    rng = np.random.default_rng(U + width)
+    H = np.zeros(U, dtype=np.uint32)
+    nz = rng.choice(U, size=max(1, U // 40), replace=False)
+    H[nz] = rng.integers(1, 5, size=nz.size)
+    mid = rng.choice(U, size=max(1, U // 2000), replace=False)
+    H[mid] = rng.integers(5, 300, size=mid.size)
+    H[rng.integers(0, U)] += U // 16
+    n = int(H.sum())
+    cap = {"exact": n, "larger": n + n // 8, "smaller": n - n // 2}[cap_kind]
+    assert 4 * cap < U
+    fill = 0xBEEF if width == 2 else 0xDEADBEEF
+    out = dev(np.full(cap, fill, dtype=np.uint16 if width == 2 else np.uint32))
+    ds.reconstruct(dev(H), U, cap, out=out)
+    assert ds.stream_status() == (ds.ERR_OVERFLOW if cap < n else ds.OK)
+    want = oracle.reconstruct(H, U, width=width)
+    got = host(out, np.uint16 if width == 2 else np.uint32)
+    np.testing.assert_array_equal(got[:min(cap, n)], want[:min(cap, n)])
+    if cap > n:
+        assert np.all(got[n:] == fill)  # past sum(H) nothing is written
+
+
 @pytest.mark.parametrize("U", [1, 300, 65536])
 @pytest.mark.parametrize("offset", [0, 1, 5])
 def test_reconstruct_u16_and_unaligned_out(ds, U, offset):
