@@ -714,8 +714,9 @@ def main():
     ws = torch.empty(ds.sort_workspace_size(n, U), dtype=torch.uint8, device="cuda")
     plan = ds.plan_histogram(n, U, w)
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    # kernels of ours per sort: ingestion (1, or partition + plan + split + count for two-level), offsets, expand
-    launches_per_step = (4 if plan["regime_name"] == "two_level" else 1) + 2
+    # kernels of ours per sort: two-level: partition, split, schedule, counting fused with the projection;
+    # otherwise the ingestion kernel and the (fused offsets + expansion) projection kernel
+    launches_per_step = 4 if plan["regime_name"] == "two_level" else 2
     H = torch.empty(U, dtype=torch.int32, device="cuda")
     rws = torch.empty(ds.reconstruct_workspace_size(U, n), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()

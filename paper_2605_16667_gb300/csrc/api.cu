@@ -227,6 +227,23 @@ dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, ui
     return from_cuda(launch_small_sort(kp, key_bytes, n, U, H, const_cast<void*>(op), base + hb, recon_layout(U, n),
                                        *dev, dev->err, st));
   }
+  if (key_bytes == 4 && (cfg == nullptr || cfg->regime == DIALSORT_REGIME_AUTO) && ib != 0) {
+    // the two-level form, where the planner takes it: counting fused with the projection
+    const DeviceInfo* dev = device_info();
+    if (!dev) return DIALSORT_ERR_CUDA;
+    const void *kp, *op;
+    bool keys_in_host = false;
+    if ((s = kernel_address(keys, *dev, &kp, &keys_in_host)) != DIALSORT_OK) return s;
+    if ((s = kernel_address(out, *dev, &op)) != DIALSORT_OK) return s;
+    HistPlan plan;
+    if ((s = plan_histogram(n, U, key_bytes, cfg ? cfg->skew : 0u, cfg, *dev, &plan)) != DIALSORT_OK) return s;
+    const bool two_level = plan.tuned ? plan.regime == DIALSORT_REGIME_TWO_LEVEL
+                                      : (plan.regime == DIALSORT_REGIME_GLOBAL_CRN || plan.regime == DIALSORT_REGIME_GLOBAL);
+    if (two_level && !keys_in_host && hier_fits(n, U, key_bytes, kp) && ib >= hier_layout(n, U).total)
+      return from_cuda(launch_hier_sort(static_cast<const uint32_t*>(kp), n, U, H,
+                                        static_cast<uint32_t*>(const_cast<void*>(op)), base + hb + rb,
+                                        hier_layout(n, U), *dev, dev->err, st));
+  }
   s = histogram_impl(keys, key_bytes, n, U, H, cfg, ib ? base + hb + rb : nullptr, ib, st);
   if (s != DIALSORT_OK) return s;
   return reconstruct_impl(H, U, out, key_bytes, n, base + hb, rb, st);

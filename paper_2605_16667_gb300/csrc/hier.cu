@@ -35,6 +35,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "recon_device.cuh"
 
 namespace dialsort {
 
@@ -345,17 +346,163 @@ constexpr uint64_t kSharedShare = 8;
 
 __device__ __forceinline__ bool shared_bucket(uint64_t nb, uint64_t N, uint32_t G) { return nb * G > kSharedShare * N; }
 
+// Pass-2 shared memory besides the 2^15-bin histogram (dynamic).
+struct P2Smem {
+  uint32_t wred[kP2Threads / 32];
+  uint32_t cpre[kP2Threads + 2];  // first chunk of each non-empty segment of the window, then the window's
+                                  // chunk count and a sentinel
+  uint32_t csw[kP2Threads];       // their segment words
+  uint16_t ctile[kP2Threads];     // their tiles, relative to the window
+};
+
+// Counts the low parts of bucket b in tiles [ta, tb) into hist (zeroed here, 2^15 bins).  On return hist
+// is complete, visible to the whole CTA and fenced for a bulk copy to read it.  Windows of up to 1024
+// tiles: one block scan numbers the window's non-empty segments and their chunks (16-byte pieces, 8 low
+// parts each) flat; every warp then takes an equal contiguous range of chunks.  Within a warp step lane
+// l takes chunk j0 + l: the segment boundaries falling inside the step are gathered into a 32-bit mask
+// (one boundary per lane, redux.or), and a popcount of the mask below bit l gives the lane's segment.
+__device__ __forceinline__ void count_piece(const uint16_t* __restrict__ low, const uint32_t* __restrict__ seg,
+                                            uint32_t b, uint64_t ta, uint64_t tb, uint64_t num_tiles, uint32_t S_t,
+                                            uint32_t* hist, P2Smem& sm) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  constexpr uint32_t bins = 1u << kLow;
+  for (uint32_t i = tid * 4u; i < bins; i += kP2Threads * 4u) *reinterpret_cast<uint4*>(hist + i) = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  // a stored low part is the key's low 16 bits: bit 15 is the bucket's low bit
+  const uint32_t hb_a = smem_addr(hist) - ((b & 1u) << kLow) * 4u;
+  const uint32_t* row = seg + (uint64_t)b * num_tiles;
+  uint32_t rkey = 0, rcnt = 0;
+  for (uint64_t w0 = ta; w0 < tb; w0 += kP2Threads) {
+    const uint32_t nw = (uint32_t)min((uint64_t)kP2Threads, tb - w0);
+    const uint32_t sgw = tid < nw ? row[w0 + tid] : 0u;
+    const uint32_t ch = ((sgw >> 16) + 7u) >> 3;
+    const uint32_t packed = (ch << 11) | (ch ? 1u : 0u);  // chunks (21 bits) | non-empty segments (11 bits)
+    uint32_t x = packed;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= (uint32_t)d) x += y;
+    }
+    __syncthreads();  // the previous window's tables are no longer read
+    if (lane == 31) sm.wred[warp] = x;
+    __syncthreads();
+    uint32_t wbase = 0, total = 0;
+    for (uint32_t w = 0; w < kP2Threads / 32; ++w) {
+      const uint32_t v = sm.wred[w];
+      if (w < warp) wbase += v;
+      total += v;
+    }
+    const uint32_t excl = wbase + x - packed;
+    if (ch) {
+      const uint32_t i = excl & 0x7ffu;
+      sm.cpre[i] = excl >> 11;
+      sm.csw[i] = sgw;
+      sm.ctile[i] = (uint16_t)tid;
+    }
+    const uint32_t nnz = total & 0x7ffu, nch = total >> 11;
+    if (tid == 0) sm.cpre[nnz] = nch;
+    if (tid == 1) sm.cpre[nnz + 1] = 0xffffffffu;  // sentinel past the last boundary
+    __syncthreads();
+    const uint32_t j_lo = (uint32_t)((uint64_t)nch * warp / (kP2Threads / 32));
+    const uint32_t j_hi = (uint32_t)((uint64_t)nch * (warp + 1) / (kP2Threads / 32));
+    if (j_lo >= j_hi) continue;
+    // the segment holding chunk j_lo: the last e with cpre[e] <= j_lo (same in every lane)
+    uint32_t e = 0;
+    for (uint32_t step = kP2Threads / 2; step != 0; step >>= 1)
+      if (e + step < nnz && sm.cpre[e + step] <= j_lo) e += step;
+    constexpr int F = 4;  // chunks in flight per lane
+    for (uint32_t j0 = j_lo; j0 < j_hi; j0 += 32u * F) {  // warp-uniform bound
+      uint4 q[F];
+      uint32_t nh[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        const uint32_t jf = j0 + 32u * f, j = jf + lane;
+        // boundaries cpre[e + 1 + k] (k = lane) inside [jf, jf + 32) -> mask bits; cpre[e + 1] >= jf
+        const uint32_t bk = sm.cpre[min(e + 1u + lane, nnz + 1u)] - jf;
+        const uint32_t m = __reduce_or_sync(0xffffffffu, bk < 32u ? 1u << bk : 0u);
+        const uint32_t idx = e + __popc(m & (0xffffffffu >> (31u - lane)));
+        e = __shfl_sync(0xffffffffu, idx, 31);
+        q[f] = make_uint4(0u, 0u, 0u, 0u);
+        nh[f] = 0;
+        if (j < j_hi) {
+          const uint32_t sgu = sm.csw[idx], c = j - sm.cpre[idx], cnt = sgu >> 16;
+          nh[f] = cnt - c * 8u >= 8u ? 8u : cnt - c * 8u;
+          q[f] = ld_stream_v4(
+              reinterpret_cast<const uint4*>(low + (w0 + sm.ctile[idx]) * (uint64_t)S_t + (sgu & 0xffffu) * 8u) + c);
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        const uint4 w = q[f];
+        // eight equal low parts: one item (key, 8), accumulated in the lane while the key repeats
+        if (nh[f] == 8u && w.x == w.y && w.x == w.z && w.x == w.w && (w.x & 0xffffu) == (w.x >> 16)) {
+          if (w.x != rkey) {
+            if (rcnt) red_s32(hb_a + (rkey & 0xffffu) * 4u, rcnt);
+            rkey = w.x;
+            rcnt = 0;
+          }
+          rcnt += 8u;
+        } else if (nh[f] == 8u) {
+          red_s32(hb_a + (w.x & 0xffffu) * 4u, 1u);
+          red_s32(hb_a + (w.x >> 16) * 4u, 1u);
+          red_s32(hb_a + (w.y & 0xffffu) * 4u, 1u);
+          red_s32(hb_a + (w.y >> 16) * 4u, 1u);
+          red_s32(hb_a + (w.z & 0xffffu) * 4u, 1u);
+          red_s32(hb_a + (w.z >> 16) * 4u, 1u);
+          red_s32(hb_a + (w.w & 0xffffu) * 4u, 1u);
+          red_s32(hb_a + (w.w >> 16) * 4u, 1u);
+        } else if (nh[f]) {
+          const uint32_t k[8] = {w.x & 0xffffu, w.x >> 16, w.y & 0xffffu, w.y >> 16,
+                                 w.z & 0xffffu, w.z >> 16, w.w & 0xffffu, w.w >> 16};
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if ((uint32_t)i < nh[f]) red_s32(hb_a + k[i] * 4u, 1u);
+        }
+      }
+    }
+  }
+  if (rcnt) red_s32(hb_a + (rkey & 0xffffu) * 4u, rcnt);
+  fence_proxy_async_smem();  // the histogram, before a bulk copy reads it
+  __syncthreads();
+}
+
+// Adds hist (bins [0, Ub) of bucket b) into H[b 2^15 ...]: bin by bin when few bins are non-zero, else
+// whole 16-byte pieces by four bulk reduce-adds (issued by threads 0-3, which then have a bulk group in
+// flight) and the ragged end bin by bin.
+__device__ __forceinline__ void flush_piece(const uint32_t* hist, uint32_t Ub, uint32_t* __restrict__ Hb,
+                                            uint32_t* wred) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  uint32_t nz = 0;
+  for (uint32_t i = tid; i < Ub; i += kP2Threads) nz += hist[i] != 0u;
+  nz = __reduce_add_sync(0xffffffffu, nz);
+  if (lane == 0) wred[warp] = nz;
+  __syncthreads();
+  nz = 0;
+#pragma unroll
+  for (uint32_t w = 0; w < kP2Threads / 32; ++w) nz += wred[w];
+  if (nz * 16u <= Ub) {
+    // few distinct keys (a hot bucket shared by many CTAs): add the non-zero bins one by one
+    for (uint32_t i = tid; i < Ub; i += kP2Threads)
+      if (hist[i]) red_add_global(Hb + i, hist[i]);
+  } else {
+    const uint32_t body = Ub & ~3u;
+    if (tid < 4) {
+      const uint32_t piece = (body / 4u) & ~3u;
+      const uint32_t a = piece * tid, z = tid == 3 ? body : piece * (tid + 1);
+      if (z > a) bulk_reduce_add_u32(Hb + a, hist + a, (z - a) * 4u);
+    }
+    for (uint32_t i = body + tid; i < Ub; i += kP2Threads)
+      if (hist[i]) red_add_global(Hb + i, hist[i]);
+  }
+}
+
 __global__ void __launch_bounds__(kP2Threads, 1) hier_count_kernel(
     const uint16_t* __restrict__ low, const uint32_t* __restrict__ seg, const uint64_t* __restrict__ start,
     const uint32_t* __restrict__ btot, uint32_t B, uint32_t U, uint64_t num_tiles, uint32_t S_t,
     uint32_t* __restrict__ H, uint32_t* __restrict__ part, uint32_t* __restrict__ part_used) {
   extern __shared__ __align__(128) uint32_t hist[];  // 2^15 bins
-  __shared__ uint32_t wred[kP2Threads / 32];
-  __shared__ uint32_t cpre[kP2Threads + 2];  // first chunk of each non-empty segment of the window, then
-                                             // the window's chunk count and a sentinel
-  __shared__ uint32_t csw[kP2Threads];       // their segment words
-  __shared__ uint16_t ctile[kP2Threads];     // their tiles, relative to the window
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  __shared__ P2Smem sm;
+  const uint32_t tid = threadIdx.x;
   constexpr uint32_t bins = 1u << kLow;
   uint64_t s = start[blockIdx.x];
   const uint64_t se = min(start[blockIdx.x + 1], (uint64_t)B * num_tiles);
@@ -370,109 +517,7 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_count_kernel(
     if (btot[b] == 0) continue;  // an empty bucket (the same value in every thread)
     if (pending && tid < 4) bulk_wait_read();
     __syncthreads();
-    for (uint32_t i = tid * 4u; i < bins; i += kP2Threads * 4u) *reinterpret_cast<uint4*>(hist + i) = make_uint4(0u, 0u, 0u, 0u);
-    __syncthreads();
-    // a stored low part is the key's low 16 bits: bit 15 is the bucket's low bit
-    const uint32_t hb_a = smem_addr(hist) - ((b & 1u) << kLow) * 4u;
-    const uint32_t* row = seg + (uint64_t)b * num_tiles;
-    uint32_t rkey = 0, rcnt = 0;
-    // Windows of up to 1024 tiles.  One block scan numbers the window's non-empty segments and their
-    // chunks (16-byte pieces, 8 low parts each) flat; every warp then takes an equal contiguous range of
-    // chunks.  Within a warp step lane l takes chunk j0 + l: the segment boundaries falling inside the
-    // step are gathered into a 32-bit mask (one boundary per lane, redux.or), and a popcount of the
-    // mask below bit l gives the lane's segment.
-    for (uint64_t w0 = ta; w0 < tb; w0 += kP2Threads) {
-      const uint32_t nw = (uint32_t)min((uint64_t)kP2Threads, tb - w0);
-      const uint32_t sgw = tid < nw ? row[w0 + tid] : 0u;
-      const uint32_t ch = ((sgw >> 16) + 7u) >> 3;
-      const uint32_t packed = (ch << 11) | (ch ? 1u : 0u);  // chunks (21 bits) | non-empty segments (11 bits)
-      uint32_t x = packed;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= (uint32_t)d) x += y;
-      }
-      __syncthreads();  // the previous window's tables are no longer read
-      if (lane == 31) wred[warp] = x;
-      __syncthreads();
-      uint32_t wbase = 0, total = 0;
-      for (uint32_t w = 0; w < kP2Threads / 32; ++w) {
-        const uint32_t v = wred[w];
-        if (w < warp) wbase += v;
-        total += v;
-      }
-      const uint32_t excl = wbase + x - packed;
-      if (ch) {
-        const uint32_t i = excl & 0x7ffu;
-        cpre[i] = excl >> 11;
-        csw[i] = sgw;
-        ctile[i] = (uint16_t)tid;
-      }
-      const uint32_t nnz = total & 0x7ffu, nch = total >> 11;
-      if (tid == 0) cpre[nnz] = nch;
-      if (tid == 1) cpre[nnz + 1] = 0xffffffffu;  // sentinel past the last boundary
-      __syncthreads();
-      const uint32_t j_lo = (uint32_t)((uint64_t)nch * warp / (kP2Threads / 32));
-      const uint32_t j_hi = (uint32_t)((uint64_t)nch * (warp + 1) / (kP2Threads / 32));
-      if (j_lo >= j_hi) continue;
-      // the segment holding chunk j_lo: the last e with cpre[e] <= j_lo (same in every lane)
-      uint32_t e = 0;
-      for (uint32_t step = kP2Threads / 2; step != 0; step >>= 1)
-        if (e + step < nnz && cpre[e + step] <= j_lo) e += step;
-      constexpr int F = 4;  // chunks in flight per lane
-      for (uint32_t j0 = j_lo; j0 < j_hi; j0 += 32u * F) {  // warp-uniform bound
-        uint4 q[F];
-        uint32_t nh[F];
-#pragma unroll
-        for (int f = 0; f < F; ++f) {
-          const uint32_t jf = j0 + 32u * f, j = jf + lane;
-          // boundaries cpre[e + 1 + k] (k = lane) inside [jf, jf + 32) -> mask bits; cpre[e + 1] >= jf
-          const uint32_t bk = cpre[min(e + 1u + lane, nnz + 1u)] - jf;
-          const uint32_t m = __reduce_or_sync(0xffffffffu, bk < 32u ? 1u << bk : 0u);
-          const uint32_t idx = e + __popc(m & (0xffffffffu >> (31u - lane)));
-          e = __shfl_sync(0xffffffffu, idx, 31);
-          q[f] = make_uint4(0u, 0u, 0u, 0u);
-          nh[f] = 0;
-          if (j < j_hi) {
-            const uint32_t sgu = csw[idx], c = j - cpre[idx], cnt = sgu >> 16;
-            nh[f] = cnt - c * 8u >= 8u ? 8u : cnt - c * 8u;
-            q[f] = ld_stream_v4(
-                reinterpret_cast<const uint4*>(low + (w0 + ctile[idx]) * (uint64_t)S_t + (sgu & 0xffffu) * 8u) + c);
-          }
-        }
-#pragma unroll
-        for (int f = 0; f < F; ++f) {
-          const uint4 w = q[f];
-          // eight equal low parts: one item (key, 8), accumulated in the lane while the key repeats
-          if (nh[f] == 8u && w.x == w.y && w.x == w.z && w.x == w.w && (w.x & 0xffffu) == (w.x >> 16)) {
-            if (w.x != rkey) {
-              if (rcnt) red_s32(hb_a + (rkey & 0xffffu) * 4u, rcnt);
-              rkey = w.x;
-              rcnt = 0;
-            }
-            rcnt += 8u;
-          } else if (nh[f] == 8u) {
-            red_s32(hb_a + (w.x & 0xffffu) * 4u, 1u);
-            red_s32(hb_a + (w.x >> 16) * 4u, 1u);
-            red_s32(hb_a + (w.y & 0xffffu) * 4u, 1u);
-            red_s32(hb_a + (w.y >> 16) * 4u, 1u);
-            red_s32(hb_a + (w.z & 0xffffu) * 4u, 1u);
-            red_s32(hb_a + (w.z >> 16) * 4u, 1u);
-            red_s32(hb_a + (w.w & 0xffffu) * 4u, 1u);
-            red_s32(hb_a + (w.w >> 16) * 4u, 1u);
-          } else if (nh[f]) {
-            const uint32_t k[8] = {w.x & 0xffffu, w.x >> 16, w.y & 0xffffu, w.y >> 16,
-                                   w.z & 0xffffu, w.z >> 16, w.w & 0xffffu, w.w >> 16};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if ((uint32_t)i < nh[f]) red_s32(hb_a + k[i] * 4u, 1u);
-          }
-        }
-      }
-    }
-    if (rcnt) red_s32(hb_a + (rkey & 0xffffu) * 4u, rcnt);
-    fence_proxy_async_smem();  // the histogram, before a bulk reduce reads it
-    __syncthreads();
+    count_piece(low, seg, b, ta, tb, num_tiles, S_t, hist, sm);
     const uint64_t blo = (uint64_t)b << kLow;
     const uint32_t Ub = (uint32_t)min((uint64_t)bins, (uint64_t)U - blo);
     if (shared_bucket(btot[b], N, gridDim.x)) {
@@ -485,29 +530,8 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_count_kernel(
       if (tid == 0) part_used[slot] = b + 1u;  // slots of neighbouring buckets interleave: tag the bucket
       continue;
     }
-    uint32_t nz = 0;
-    for (uint32_t i = tid; i < Ub; i += kP2Threads) nz += hist[i] != 0u;
-    nz = __reduce_add_sync(0xffffffffu, nz);
-    if (lane == 0) wred[warp] = nz;
-    __syncthreads();
-    nz = 0;
-#pragma unroll
-    for (uint32_t w = 0; w < kP2Threads / 32; ++w) nz += wred[w];
-    if (nz * 16u <= Ub) {
-      // few distinct keys (a hot bucket shared by many CTAs): add the non-zero bins one by one
-      for (uint32_t i = tid; i < Ub; i += kP2Threads)
-        if (hist[i]) red_add_global(H + blo + i, hist[i]);
-    } else {
-      const uint32_t body = Ub & ~3u;  // whole 16-byte pieces go by bulk reduce-add, in four parts
-      if (tid < 4) {
-        const uint32_t piece = (body / 4u) & ~3u;
-        const uint32_t a = piece * tid, z = tid == 3 ? body : piece * (tid + 1);
-        if (z > a) bulk_reduce_add_u32(H + blo + a, hist + a, (z - a) * 4u);
-        pending = true;
-      }
-      for (uint32_t i = body + tid; i < Ub; i += kP2Threads)
-        if (hist[i]) red_add_global(H + blo + i, hist[i]);
-    }
+    flush_piece(hist, Ub, H + blo, sm.wred);
+    pending = true;
   }
   if (tid < 4) bulk_wait_all();
 }
@@ -549,6 +573,218 @@ __global__ void __launch_bounds__(256) hier_merge_kernel(const uint32_t* __restr
     if (i0 + j < Ub) H[blo + i0 + j] += a[j];  // the only writer of these bins
 }
 
+// ---------------------------------------------------------------- sort: counting fused with the projection
+//
+// For a sort, pass 2 and the projection (Eq. (2)) run in one persistent kernel whose CTAs take work
+// items in one ticket order: count ranges of the bucket-major segment sequence (pass 2 as above, every
+// piece reduce-added into H), interleaved with projection items -- one 1024-bin chunk of H each, which
+// writes the chunk's runs of the output.  A bucket's projection items are placed after the last count
+// range that touches the bucket (plus a delay of one grid's worth of tickets), so earlier buckets are
+// projected while later ones are still being counted: the output writes overlap the low-part reads.
+// A projection item waits (bounded) until every piece of its bucket has been added into H, then finds
+// its chunk's start by decoupled look-back over the bucket's earlier chunks (a bucket's first key lands
+// at the sum of the earlier buckets' keys, known from pass 1).  Every wait is for items with smaller
+// tickets, which running CTAs hold: the waits end whatever the number of resident CTAs.
+constexpr uint32_t kFusedMaxRanges = 1024;
+constexpr uint32_t kChunksPerBucket = (1u << kLow) / kChunkBins;  // 32
+constexpr uint32_t kFusedMaxChunks = kMaxBuckets * kChunksPerBucket;
+constexpr uint32_t kProjItem = 0x80000000u;
+constexpr uint32_t kNoItem = 0xffffffffu;
+
+struct FusedCtl {
+  uint32_t ticket;
+  uint32_t nsched;
+};
+
+// One CTA: pieces[b] (count ranges that touch non-empty bucket b), bbase[b] (keys of buckets < b), and the
+// item order sched[0 .. nsched): range k as k, chunk c of the projection as kProjItem | c.
+__global__ void __launch_bounds__(1024) hier_sched_kernel(const uint64_t* __restrict__ start, uint32_t K,
+                                                          const uint32_t* __restrict__ btot, uint32_t B, uint32_t U,
+                                                          uint64_t num_tiles, uint32_t delay, uint32_t* sched,
+                                                          uint32_t* pieces, uint64_t* bbase, FusedCtl* ctl) {
+  __shared__ uint32_t s_r[kMaxBuckets], s_nch[kMaxBuckets], s_off[kMaxBuckets], s_bt[kMaxBuckets];
+  __shared__ uint64_t s_start[kFusedMaxRanges + 1];
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t k = tid; k <= K; k += blockDim.x) s_start[k] = start[k];  // one round trip, then shared memory
+  if (tid < B) s_bt[tid] = btot[tid];
+  __syncthreads();
+  if (tid < B) {
+    const uint32_t b = tid;
+    const uint64_t lo = (uint64_t)b * num_tiles, hi = lo + num_tiles;
+    uint32_t l = 0, r = K;  // first range whose end lies past the bucket's first tile
+    while (l < r) {
+      const uint32_t m = (l + r) / 2;
+      if (s_start[m + 1] > lo)
+        r = m;
+      else
+        l = m + 1;
+    }
+    uint32_t cnt = 0, klast = 0;
+    for (uint32_t k = l; k < K && s_start[k] < hi; ++k)
+      if (s_start[k] < s_start[k + 1]) {
+        ++cnt;
+        klast = k;
+      }
+    const bool full = s_bt[b] != 0;
+    pieces[b] = full ? cnt : 0u;
+    s_r[b] = min(K - 1u, klast + delay);
+    const uint32_t ub = (uint32_t)min((uint64_t)1u << kLow, (uint64_t)U - ((uint64_t)b << kLow));
+    s_nch[b] = full ? (ub + kChunkBins - 1) / kChunkBins : 0u;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t o = 0;
+    uint64_t kb = 0;
+    for (uint32_t b = 0; b < B; ++b) {
+      s_off[b] = o;
+      o += s_nch[b];
+      bbase[b] = kb;
+      kb += s_bt[b];
+    }
+    ctl->nsched = K + o;
+  }
+  __syncthreads();
+  for (uint32_t t = tid; t < K; t += blockDim.x) {
+    uint32_t idx = t;
+    for (uint32_t b = 0; b < B; ++b)
+      if (s_r[b] < t) idx += s_nch[b];
+    sched[idx] = t;
+  }
+  for (uint32_t b = 0; b < B; ++b) {
+    const uint32_t at = s_r[b] + 1u + s_off[b];
+    for (uint32_t j = tid; j < s_nch[b]; j += blockDim.x) sched[at + j] = kProjItem | (b * kChunksPerBucket + j);
+  }
+}
+
+// Projection item: chunk c (bins [1024 c, 1024 c + 1024)), one bin per thread.
+__device__ __forceinline__ void project_chunk(uint32_t c, const uint32_t* __restrict__ H, uint32_t U,
+                                              const uint32_t* __restrict__ pieces, const uint32_t* bdone,
+                                              const uint64_t* __restrict__ bbase, uint64_t* desc, uint32_t* out,
+                                              uint64_t n_cap, int out_aligned, uint32_t* err, uint32_t* red,
+                                              uint64_t* s_pre) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t b = c / kChunksPerBucket, j = c % kChunksPerBucket;
+  if (tid == 0) {  // every piece of the bucket is in H
+    uint32_t spins = 0;
+    const uint32_t need = pieces[b];
+    while (ld_acquire_u32(bdone + b) < need) {
+      if (++spins > kSpinLimit) {
+        raise_error(err, ERRBIT_TIMEOUT);
+        break;
+      }
+      __nanosleep(128);
+    }
+  }
+  __syncthreads();
+  const uint64_t bin = (uint64_t)c * kChunkBins + tid;
+  const uint32_t h = (tid < kChunkBins && bin < U) ? __ldcg(H + bin) : 0u;
+  // block exclusive scan of the bins (a warp scan, then the warp totals)
+  uint32_t x = h;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= (uint32_t)d) x += y;
+  }
+  if (lane == 31) red[warp] = x;
+  __syncthreads();
+  uint32_t wb = 0, total = 0;
+  for (uint32_t w = 0; w < kP2Threads / 32; ++w) {
+    const uint32_t v = red[w];
+    if (w < warp) wb += v;
+    total += v;
+  }
+  const uint32_t excl = wb + x - h;
+  if (tid == 0) {  // the chunk's start within its bucket: decoupled look-back over the bucket's chunks
+    uint64_t pre = 0;
+    if (j == 0) {
+      st_release_u64(desc + c, kFlagInc | total);
+    } else {
+      st_release_u64(desc + c, kFlagAgg | total);
+      uint32_t k = c - 1, spins = 0;
+      for (;;) {
+        const uint64_t d = ld_acquire_u64(desc + k);
+        const uint64_t flag = d & ~kValMask;
+        if (flag == 0) {
+          if (++spins > kSpinLimit) {
+            raise_error(err, ERRBIT_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+          continue;
+        }
+        pre += d & kValMask;
+        if (flag == kFlagInc || k % kChunksPerBucket == 0) break;
+        --k;
+      }
+      st_release_u64(desc + c, kFlagInc | ((pre + total) & kValMask));
+    }
+    *s_pre = bbase[b] + pre;
+  }
+  __syncthreads();
+  const uint64_t st = *s_pre + excl, en = min(st + h, n_cap);
+  // a lane writes its run when short; longer runs are painted by the whole warp
+  if (h != 0 && h <= 4u)
+    for (uint64_t p = st; p < en; ++p) out[p] = (uint32_t)bin;
+  uint32_t lanes = __ballot_sync(0xffffffffu, h > 4u && st < en);
+  while (lanes) {
+    const uint32_t src = (uint32_t)(__ffs(lanes) - 1);
+    lanes &= lanes - 1;
+    const uint64_t s0 = __shfl_sync(0xffffffffu, st, src), e0 = __shfl_sync(0xffffffffu, en, src);
+    paint_run<uint32_t>(out, (uint32_t)s0, (uint32_t)e0, (uint32_t)(c * kChunkBins + src + warp * 32u), out_aligned,
+                        lane, 32u);
+  }
+}
+
+__global__ void __launch_bounds__(kP2Threads, 1) hier_sort_kernel(
+    const uint16_t* __restrict__ low, const uint32_t* __restrict__ seg, const uint64_t* __restrict__ start,
+    const uint32_t* __restrict__ btot, uint32_t B, uint32_t U, uint64_t num_tiles, uint32_t S_t,
+    uint32_t* __restrict__ H, const uint32_t* __restrict__ sched, const uint32_t* __restrict__ pieces,
+    uint32_t* bdone, const uint64_t* __restrict__ bbase, uint64_t* desc, uint32_t* __restrict__ out, uint64_t n_cap,
+    int out_aligned, FusedCtl* ctl, uint32_t* err) {
+  extern __shared__ __align__(128) uint32_t hist[];  // 2^15 bins
+  __shared__ P2Smem sm;
+  __shared__ uint32_t s_item;
+  __shared__ uint64_t s_pre;
+  const uint32_t tid = threadIdx.x;
+  constexpr uint32_t bins = 1u << kLow;
+  const uint32_t nsched = ctl->nsched;
+  for (;;) {
+    __syncthreads();  // the previous item is done with the shared words
+    if (tid == 0) {
+      const uint32_t t = atomicAdd(&ctl->ticket, 1u);
+      s_item = t < nsched ? sched[t] : kNoItem;
+    }
+    __syncthreads();
+    const uint32_t w = s_item;
+    if (w == kNoItem) break;
+    if (w & kProjItem) {
+      project_chunk(w & ~kProjItem, H, U, pieces, bdone, bbase, desc, out, n_cap, out_aligned, err, sm.wred, &s_pre);
+      continue;
+    }
+    uint64_t s = start[w];
+    const uint64_t se = min(start[w + 1], (uint64_t)B * num_tiles);
+    while (s < se) {
+      const uint32_t b = (uint32_t)(s / num_tiles);
+      const uint64_t ta = s - (uint64_t)b * num_tiles;
+      const uint64_t tb = min(num_tiles, ta + (se - s));
+      s += tb - ta;
+      if (btot[b] == 0) continue;  // an empty bucket (the same value in every thread)
+      __syncthreads();
+      count_piece(low, seg, b, ta, tb, num_tiles, S_t, hist, sm);
+      const uint64_t blo = (uint64_t)b << kLow;
+      flush_piece(hist, (uint32_t)min((uint64_t)bins, (uint64_t)U - blo), H + blo, sm.wred);
+      // the piece is in H (bulk adds complete and ordered before the release) before it is counted
+      if (tid < 4) {
+        bulk_wait_all();
+        fence_proxy_async_global();
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(bdone + b, 1u);
+    }
+  }
+}
+
 }  // namespace
 
 HierLayout hier_layout(uint64_t n, uint32_t U) {
@@ -571,6 +807,17 @@ HierLayout hier_layout(uint64_t n, uint32_t U) {
   o = align_up(o + 4 * ((size_t)T.G_max + T.B), 256);
   T.off_part = o;
   o = align_up(o + 4 * ((size_t)T.G_max + T.B) * (1u << kLow), 256);
+  T.off_fclear = o;  // FusedCtl | bucket counters | one descriptor per 1024-bin chunk
+  o = align_up(o + 256 + 4 * (size_t)kMaxBuckets + 8 * (size_t)kFusedMaxChunks, 256);
+  T.fclear_bytes = o - T.off_fclear;
+  T.off_fstart = o;
+  o = align_up(o + 8 * ((size_t)kFusedMaxRanges + 1), 256);
+  T.off_sched = o;
+  o = align_up(o + 4 * ((size_t)kFusedMaxRanges + kFusedMaxChunks), 256);
+  T.off_pieces = o;
+  o = align_up(o + 4 * (size_t)kMaxBuckets, 256);
+  T.off_bbase = o;
+  o = align_up(o + 8 * (size_t)kMaxBuckets, 256);
   T.total = o;
   return T;
 }
@@ -589,15 +836,13 @@ bool hier_fits(uint64_t n, uint32_t U, uint32_t key_bytes, const void* keys) {
   return (reinterpret_cast<uintptr_t>(keys) & 15u) == 0 && hier_shape_fits(n, U, key_bytes);
 }
 
-cudaError_t launch_hier(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* ws, const HierLayout& T,
-                        const DeviceInfo& dev, uint32_t* err, cudaStream_t stream, bool accumulate) {
-  char* base = static_cast<char*>(ws);
+namespace {
+// Pass 1: bucket totals cleared, then the partition of every tile.
+cudaError_t launch_partition(const uint32_t* keys, uint64_t n, uint32_t U, char* base, const HierLayout& T,
+                             const DeviceInfo& dev, uint32_t* err, cudaStream_t stream) {
   uint16_t* low = reinterpret_cast<uint16_t*>(base + T.off_low);
   uint32_t* seg = reinterpret_cast<uint32_t*>(base + T.off_seg);
   uint32_t* btot = reinterpret_cast<uint32_t*>(base + T.off_btot);
-  uint64_t* start = reinterpret_cast<uint64_t*>(base + T.off_start);
-  uint32_t* part_used = reinterpret_cast<uint32_t*>(base + T.off_used);
-  uint32_t* part = reinterpret_cast<uint32_t*>(base + T.off_part);
   cudaError_t e = cudaMemsetAsync(btot, 0, 4 * (size_t)kMaxBuckets, stream);
   if (e != cudaSuccess) return e;
   const bool pow2 = (U & (U - 1)) == 0;
@@ -614,8 +859,22 @@ cudaError_t launch_hier(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* 
     uint64_t nn = n, nt = T.num_tiles;
     void* args[] = {const_cast<uint32_t**>(&keys), &nn, &UU, &B, &nt, &S_t, &low, &seg, &btot, &err};
     e = cudaLaunchKernel(p1, dim3((unsigned)grid1), dim3(kP1Threads), args, 0, stream);
-    if (e != cudaSuccess) return e;
   }
+  return e;
+}
+}  // namespace
+
+cudaError_t launch_hier(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* ws, const HierLayout& T,
+                        const DeviceInfo& dev, uint32_t* err, cudaStream_t stream, bool accumulate) {
+  char* base = static_cast<char*>(ws);
+  uint16_t* low = reinterpret_cast<uint16_t*>(base + T.off_low);
+  uint32_t* seg = reinterpret_cast<uint32_t*>(base + T.off_seg);
+  uint32_t* btot = reinterpret_cast<uint32_t*>(base + T.off_btot);
+  uint64_t* start = reinterpret_cast<uint64_t*>(base + T.off_start);
+  uint32_t* part_used = reinterpret_cast<uint32_t*>(base + T.off_used);
+  uint32_t* part = reinterpret_cast<uint32_t*>(base + T.off_part);
+  cudaError_t e = launch_partition(keys, n, U, base, T, dev, err, stream);
+  if (e != cudaSuccess) return e;
   const uint32_t G = hier_count_ctas(n, (uint32_t)dev.sms);
   hier_split_kernel<<<T.B, 1024, 0, stream>>>(seg, btot, T.B, T.num_tiles, G, start);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -628,6 +887,42 @@ cudaError_t launch_hier(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* 
                                                         part_used);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   hier_merge_kernel<<<dim3(T.B, (1u << kLow) / 1024u), 256, 0, stream>>>(btot, T.B, U, G, part, part_used, H);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hier_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, uint32_t* out, void* ws,
+                             const HierLayout& T, const DeviceInfo& dev, uint32_t* err, cudaStream_t stream) {
+  char* base = static_cast<char*>(ws);
+  const uint16_t* low = reinterpret_cast<const uint16_t*>(base + T.off_low);
+  const uint32_t* seg = reinterpret_cast<const uint32_t*>(base + T.off_seg);
+  const uint32_t* btot = reinterpret_cast<const uint32_t*>(base + T.off_btot);
+  FusedCtl* ctl = reinterpret_cast<FusedCtl*>(base + T.off_fclear);
+  uint32_t* bdone = reinterpret_cast<uint32_t*>(base + T.off_fclear + 256);
+  uint64_t* desc = reinterpret_cast<uint64_t*>(base + T.off_fclear + 256 + 4 * (size_t)kMaxBuckets);
+  uint64_t* start = reinterpret_cast<uint64_t*>(base + T.off_fstart);
+  uint32_t* sched = reinterpret_cast<uint32_t*>(base + T.off_sched);
+  uint32_t* pieces = reinterpret_cast<uint32_t*>(base + T.off_pieces);
+  uint64_t* bbase = reinterpret_cast<uint64_t*>(base + T.off_bbase);
+  cudaError_t e = launch_partition(keys, n, U, base, T, dev, err, stream);
+  if (e != cudaSuccess) return e;
+  // count ranges: about four per SM (so that early buckets finish, and are projected, while later ones
+  // are counted), at least 2^17 keys each
+  const uint32_t K = (uint32_t)std::min<uint64_t>(
+      std::min<uint64_t>(kFusedMaxRanges, 4ull * std::max(dev.sms, 1)), std::max<uint64_t>(1, n >> 17));
+  hier_split_kernel<<<T.B, 1024, 0, stream>>>(seg, btot, T.B, T.num_tiles, K, start);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(H, 0, (size_t)U * 4, stream)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(base + T.off_fclear, 0, T.fclear_bytes, stream)) != cudaSuccess) return e;
+  const size_t smem = (size_t)4 << kLow;
+  int per_sm = 0;
+  e = kernel_config(reinterpret_cast<const void*>(&hier_sort_kernel), kP2Threads, smem, false, &per_sm);
+  if (e != cudaSuccess) return e;
+  const uint32_t grid = (uint32_t)std::max(1, dev.sms * std::max(per_sm, 1));
+  hier_sched_kernel<<<1, 1024, 0, stream>>>(start, K, btot, T.B, U, T.num_tiles, grid, sched, pieces, bbase, ctl);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int aligned = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+  hier_sort_kernel<<<grid, kP2Threads, smem, stream>>>(low, seg, start, btot, T.B, U, T.num_tiles, T.S_t, H, sched,
+                                                      pieces, bdone, bbase, desc, out, n, aligned, ctl, err);
   return cudaGetLastError();
 }
 

@@ -92,6 +92,9 @@ struct HierLayout {
   uint32_t S_t = 0;              // staged entries per tile in the workspace
   uint32_t G_max = 0;            // pass-2 CTAs the scratch has room for
   size_t off_low = 0, off_seg = 0, off_btot = 0, off_start = 0, off_used = 0, off_part = 0;
+  // the sort's fused count + projection: cleared words (ticket, bucket counters, look-back descriptors),
+  // then its count ranges, item order, pieces per bucket and bucket bases
+  size_t off_fclear = 0, fclear_bytes = 0, off_fstart = 0, off_sched = 0, off_pieces = 0, off_bbase = 0;
   size_t total = 0;
 };
 constexpr uint32_t kHierMaxCountCtas = 256;  // pass-2 CTAs (one per SM) at most
@@ -102,6 +105,10 @@ bool hier_shape_fits(uint64_t n, uint32_t U, uint32_t key_bytes);
 bool hier_fits(uint64_t n, uint32_t U, uint32_t key_bytes, const void* keys);
 cudaError_t launch_hier(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, void* ws, const HierLayout& T,
                         const DeviceInfo& dev, uint32_t* err, cudaStream_t stream, bool accumulate);
+// The whole sort of uint32 keys in the two-level form: pass 1, then counting fused with the projection
+// (Eq. (2)) into out (n_cap keys); H receives the histogram.
+cudaError_t launch_hier_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, uint32_t* out, void* ws,
+                             const HierLayout& T, const DeviceInfo& dev, uint32_t* err, cudaStream_t stream);
 
 // Self-tests of the bounded device waits (a wait that is made to run out).
 size_t offsets_selftest_bytes();
