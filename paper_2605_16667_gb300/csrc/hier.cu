@@ -594,6 +594,21 @@ constexpr uint32_t kNoItem = 0xffffffffu;
 struct FusedCtl {
   uint32_t ticket;
   uint32_t nsched;
+  uint32_t nlong;    // runs longer than kWarpRun keys, left to hier_long_kernel
+  uint32_t npieces;  // their pieces of kLongPiece keys
+};
+
+// A run of more than kWarpRun keys (a hot key) is not painted by the chunk item's warp: one warp (one
+// SM) would write it alone.  It goes to a list instead, cut into pieces of kLongPiece keys that
+// hier_long_kernel paints with every SM after the fused kernel.  A chunk holding more than kChunkBudget
+// keys (skewed keys: thousands of runs of thousands of keys) lists every run of more than kListRun keys,
+// so that no chunk item writes more than about kChunkBudget keys itself.
+constexpr uint32_t kWarpRun = 8192;
+constexpr uint32_t kListRun = 512;
+constexpr uint32_t kChunkBudget = 1u << 20;
+constexpr uint32_t kLongPiece = 32768;
+struct LongRun {
+  uint32_t start, len, key, piece0;
 };
 
 // One CTA: pieces[b] (count ranges that touch non-empty bucket b), bbase[b] (keys of buckets < b), and the
@@ -660,8 +675,8 @@ __global__ void __launch_bounds__(1024) hier_sched_kernel(const uint64_t* __rest
 __device__ __forceinline__ void project_chunk(uint32_t c, const uint32_t* __restrict__ H, uint32_t U,
                                               const uint32_t* __restrict__ pieces, const uint32_t* bdone,
                                               const uint64_t* __restrict__ bbase, uint64_t* desc, uint32_t* out,
-                                              uint64_t n_cap, int out_aligned, uint32_t* err, uint32_t* red,
-                                              uint64_t* s_pre) {
+                                              uint64_t n_cap, int out_aligned, FusedCtl* ctl, LongRun* longs,
+                                              uint32_t* pmap, uint32_t* err, uint32_t* red, uint64_t* s_pre) {
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t b = c / kChunksPerBucket, j = c % kChunksPerBucket;
   if (tid == 0) {  // every piece of the bucket is in H
@@ -722,10 +737,18 @@ __device__ __forceinline__ void project_chunk(uint32_t c, const uint32_t* __rest
   }
   __syncthreads();
   const uint64_t st = *s_pre + excl, en = min(st + h, n_cap);
-  // a lane writes its run when short; longer runs are painted by the whole warp
+  // a lane writes its run when short; longer runs are painted by the whole warp; the longest are listed
+  // for hier_long_kernel
   if (h != 0 && h <= 4u)
     for (uint64_t p = st; p < en; ++p) out[p] = (uint32_t)bin;
-  uint32_t lanes = __ballot_sync(0xffffffffu, h > 4u && st < en);
+  const uint32_t list_over = total > kChunkBudget ? kListRun : kWarpRun;  // the same in every thread
+  if (h > list_over && st < en) {
+    const uint32_t len = (uint32_t)(en - st), pieces_k = (len + kLongPiece - 1) / kLongPiece;
+    const uint32_t i = atomicAdd(&ctl->nlong, 1u), p0 = atomicAdd(&ctl->npieces, pieces_k);
+    longs[i] = LongRun{(uint32_t)st, len, (uint32_t)bin, p0};
+    for (uint32_t q = 0; q < pieces_k; ++q) pmap[p0 + q] = i;
+  }
+  uint32_t lanes = __ballot_sync(0xffffffffu, h > 4u && h <= list_over && st < en);
   while (lanes) {
     const uint32_t src = (uint32_t)(__ffs(lanes) - 1);
     lanes &= lanes - 1;
@@ -740,7 +763,7 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_sort_kernel(
     const uint32_t* __restrict__ btot, uint32_t B, uint32_t U, uint64_t num_tiles, uint32_t S_t,
     uint32_t* __restrict__ H, const uint32_t* __restrict__ sched, const uint32_t* __restrict__ pieces,
     uint32_t* bdone, const uint64_t* __restrict__ bbase, uint64_t* desc, uint32_t* __restrict__ out, uint64_t n_cap,
-    int out_aligned, FusedCtl* ctl, uint32_t* err) {
+    int out_aligned, FusedCtl* ctl, LongRun* longs, uint32_t* pmap, uint32_t* err) {
   extern __shared__ __align__(128) uint32_t hist[];  // 2^15 bins
   __shared__ P2Smem sm;
   __shared__ uint32_t s_item;
@@ -758,7 +781,8 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_sort_kernel(
     const uint32_t w = s_item;
     if (w == kNoItem) break;
     if (w & kProjItem) {
-      project_chunk(w & ~kProjItem, H, U, pieces, bdone, bbase, desc, out, n_cap, out_aligned, err, sm.wred, &s_pre);
+      project_chunk(w & ~kProjItem, H, U, pieces, bdone, bbase, desc, out, n_cap, out_aligned, ctl, longs, pmap,
+                    err, sm.wred, &s_pre);
       continue;
     }
     uint64_t s = start[w];
@@ -772,6 +796,8 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_sort_kernel(
       __syncthreads();
       count_piece(low, seg, b, ta, tb, num_tiles, S_t, hist, sm);
       const uint64_t blo = (uint64_t)b << kLow;
+      // (a bucket counted by many ranges is reduce-added into H too: scratch slots summed by the projection
+      // items measured slower -- every chunk item then reads one slot per range)
       flush_piece(hist, (uint32_t)min((uint64_t)bins, (uint64_t)U - blo), H + blo, sm.wred);
       // the piece is in H (bulk adds complete and ordered before the release) before it is counted
       if (tid < 4) {
@@ -782,6 +808,20 @@ __global__ void __launch_bounds__(kP2Threads, 1) hier_sort_kernel(
       __syncthreads();
       if (tid == 0) atomicAdd(bdone + b, 1u);
     }
+  }
+}
+
+// Paints the listed runs, a piece per warp, with every SM (pieces of one run in any order).
+__global__ void __launch_bounds__(256) hier_long_kernel(const LongRun* __restrict__ longs,
+                                                        const uint32_t* __restrict__ pmap, const FusedCtl* ctl,
+                                                        uint32_t* __restrict__ out, int out_aligned) {
+  const uint32_t npieces = ctl->npieces, lane = threadIdx.x & 31u;
+  const uint32_t warps = gridDim.x * (blockDim.x / 32u);
+  for (uint32_t p = blockIdx.x * (blockDim.x / 32u) + (threadIdx.x >> 5); p < npieces; p += warps) {
+    const LongRun r = longs[pmap[p]];
+    const uint32_t s = r.start + (p - r.piece0) * kLongPiece;
+    const uint32_t e = min(s + kLongPiece, r.start + r.len);
+    paint_run<uint32_t>(out, s, e, r.key, out_aligned, lane, 32u);
   }
 }
 
@@ -818,6 +858,10 @@ HierLayout hier_layout(uint64_t n, uint32_t U) {
   o = align_up(o + 4 * (size_t)kMaxBuckets, 256);
   T.off_bbase = o;
   o = align_up(o + 8 * (size_t)kMaxBuckets, 256);
+  T.off_longs = o;  // at most n / kListRun listed runs, and n / kLongPiece + n / kListRun pieces
+  o = align_up(o + sizeof(LongRun) * (n / kListRun + 1), 256);
+  T.off_pmap = o;
+  o = align_up(o + 4 * (n / kLongPiece + n / kListRun + 1), 256);
   T.total = o;
   return T;
 }
@@ -905,10 +949,8 @@ cudaError_t launch_hier_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   uint64_t* bbase = reinterpret_cast<uint64_t*>(base + T.off_bbase);
   cudaError_t e = launch_partition(keys, n, U, base, T, dev, err, stream);
   if (e != cudaSuccess) return e;
-  // count ranges: about four per SM (so that early buckets finish, and are projected, while later ones
-  // are counted), at least 2^17 keys each
-  const uint32_t K = (uint32_t)std::min<uint64_t>(
-      std::min<uint64_t>(kFusedMaxRanges, 4ull * std::max(dev.sms, 1)), std::max<uint64_t>(1, n >> 17));
+  // count ranges: one per SM (measured faster than four: fewer pieces to flush), at least 2^17 keys each
+  const uint32_t K = hier_count_ctas(n, (uint32_t)dev.sms);
   hier_split_kernel<<<T.B, 1024, 0, stream>>>(seg, btot, T.B, T.num_tiles, K, start);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(H, 0, (size_t)U * 4, stream)) != cudaSuccess) return e;
@@ -921,8 +963,13 @@ cudaError_t launch_hier_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   hier_sched_kernel<<<1, 1024, 0, stream>>>(start, K, btot, T.B, U, T.num_tiles, grid, sched, pieces, bbase, ctl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int aligned = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+  LongRun* longs = reinterpret_cast<LongRun*>(base + T.off_longs);
+  uint32_t* pmap = reinterpret_cast<uint32_t*>(base + T.off_pmap);
   hier_sort_kernel<<<grid, kP2Threads, smem, stream>>>(low, seg, start, btot, T.B, U, T.num_tiles, T.S_t, H, sched,
-                                                      pieces, bdone, bbase, desc, out, n, aligned, ctl, err);
+                                                      pieces, bdone, bbase, desc, out, n, aligned, ctl, longs, pmap,
+                                                      err);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  hier_long_kernel<<<dev.sms * 4, 256, 0, stream>>>(longs, pmap, ctl, out, aligned);
   return cudaGetLastError();
 }
 

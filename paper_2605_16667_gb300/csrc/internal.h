@@ -95,6 +95,7 @@ struct HierLayout {
   // the sort's fused count + projection: cleared words (ticket, bucket counters, look-back descriptors),
   // then its count ranges, item order, pieces per bucket and bucket bases
   size_t off_fclear = 0, fclear_bytes = 0, off_fstart = 0, off_sched = 0, off_pieces = 0, off_bbase = 0;
+  size_t off_longs = 0, off_pmap = 0;  // runs too long for one warp, and the map of their pieces
   size_t total = 0;
 };
 constexpr uint32_t kHierMaxCountCtas = 256;  // pass-2 CTAs (one per SM) at most
