@@ -83,8 +83,8 @@ def kernel_source_hash() -> str:
 
 
 def ncu_traffic(phase: str):
-    """DRAM bytes of one launch of `phase` ("histogram" or "reconstruct") at the benchmark size, from the
-    committed ncu summary (profiles/traffic.json), only if it was taken on the current kernel sources."""
+    """DRAM bytes of one launch of kernel `phase` at the benchmark size, from the committed ncu summary
+    (profiles/traffic.json), only if it was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -784,16 +784,27 @@ def main():
     recon_ms = timed(lambda: ds.reconstruct(H, U, n, out, ws=rws, stream=stream), reps)
     expand_ms = max(recon_ms - offs_ms, 1e-9)
     peak, peak_kind = peaks()
-    hist_bytes = w * n + 8 * U   # read keys, zero H, write H
-    recon_bytes = w * n + 4 * U  # read H, write the keys
-    if hist_ms >= recon_ms:
-        dom, dom_bytes, dom_ms, kname = "histogram (zero H + ingest)", hist_bytes, hist_ms, "histogram"
+    # the kernels inside the sort itself: CUDA events between its stages (the two-level form: pass 1,
+    # split + schedule, counting fused with the projection, long runs), median of `reps` sorts
+    st_runs = np.array([ds.sort_stage_times(keys, U, out, ws, stream=stream) for _ in range(reps)])
+    stage_ms = [float(x) for x in np.median(st_runs, axis=0)]
+    if len(stage_ms) == 4:
+        stage_names = ["partition (pass 1)", "split + schedule", "count + projection (fused)", "long runs"]
+        # algorithmic bytes: pass 1 reads the keys; the fused kernel zeroes/adds/reads H and writes the keys
+        stage_bytes = [w * n, 0, w * n + 12 * U, 0]
+        kernel_of = ["hier_partition_kernel", "hier_split_kernel + hier_sched_kernel", "hier_sort_kernel",
+                     "hier_long_kernel"]
     else:
-        dom, dom_bytes, dom_ms, kname = "reconstruct (offsets + expand)", recon_bytes, recon_ms, "reconstruct"
+        stage_names, stage_bytes, kernel_of = ["sort"], [2 * w * n + 12 * U], ["sort kernels"]
+    i_dom = int(np.argmax(stage_ms))
+    dom_ms, dom_bytes = stage_ms[i_dom], stage_bytes[i_dom]
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(kname), "kernel": dom, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": dom_bytes}
+                "traffic": ncu_traffic(kernel_of[i_dom]), "kernel": f"{kernel_of[i_dom]} ({stage_names[i_dom]})",
+                "peak_source": peak_kind, "algorithmic_bytes_per_launch": dom_bytes,
+                "stages_ms": dict(zip(stage_names, stage_ms)),
+                "how": "CUDA events between the sort's stages on its stream (dialsort_sort_stage_times), median "
+                       f"of {reps} sorts after the timed region"}
     step_bytes = 2 * w * n + 12 * U
     whole = {"achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9}
     whole["frac_of_peak"] = whole["achieved_gbs"] / peak

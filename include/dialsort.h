@@ -315,6 +315,18 @@ dialsort_status_t dialsort_sort(const uint32_t* keys, uint64_t n, uint32_t U, ui
 dialsort_status_t dialsort_sort_u16(const uint16_t* keys, uint64_t n, uint32_t U, uint16_t* out, void* ws,
                                     size_t ws_bytes, void* stream);
 /*
+ * Runs dialsort_sort (key_bytes 4 or 2, automatic choices) once with CUDA
+ * events between its stages and waits for it; for measuring kernels inside
+ * a sort.  Writes the stage durations in milliseconds to ms[0 .. *stages):
+ * for the two-level form 4 stages (pass 1 partition; split and schedule;
+ * counting fused with the projection; painting of long runs), otherwise 1
+ * (the whole sort).  ms needs room for 4 values.  Arguments otherwise as
+ * dialsort_sort; synchronous.
+ */
+dialsort_status_t dialsort_sort_stage_times(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, void* out,
+                                            void* ws, size_t ws_bytes, void* stream, float* ms, uint32_t* stages);
+
+/*
  * As dialsort_sort (key_bytes 4 or 2) with explicit launch choices for step 1
  * (cfg as for dialsort_histogram_ws, NULL = automatic; its skew field feeds
  * the autotuner).  ws as for dialsort_sort.

@@ -252,6 +252,18 @@ def sort(keys: torch.Tensor, U: int, out: torch.Tensor | None = None, *, ws: tor
     return out
 
 
+def sort_stage_times(keys: torch.Tensor, U: int, out: torch.Tensor, ws: torch.Tensor, stream=None) -> list:
+    """One dialsort_sort with CUDA events between its stages (synchronous): the stage durations in ms --
+    [pass 1, split + schedule, counting fused with the projection, long runs] for the two-level form,
+    else [whole sort]."""
+    ms = (ctypes.c_float * 4)()
+    stages = ctypes.c_uint32()
+    _check(native.load().dialsort_sort_stage_times(keys.data_ptr(), _width(keys), keys.numel(), U, out.data_ptr(),
+                                                   ws.data_ptr(), ws.numel(), _stream(stream), ms,
+                                                   ctypes.byref(stages)), "dialsort_sort_stage_times")
+    return [float(ms[i]) for i in range(stages.value)]
+
+
 def histogram_accumulate(keys: torch.Tensor, U: int, H: torch.Tensor, *, ws: torch.Tensor | None = None,
                          stream=None) -> torch.Tensor:
     """Eq. (1) without zeroing: H[x] += 1 for every key x (H already holds counts).  Returns H."""

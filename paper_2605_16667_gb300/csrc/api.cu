@@ -207,7 +207,9 @@ size_t sort_h_bytes(uint32_t U) { return align_up((size_t)U * 4, 256); }
 
 // sort workspace: H | reconstruction scratch | ingestion scratch
 dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, void* out, void* ws,
-                            size_t ws_bytes, cudaStream_t st, const dialsort_hist_config_t* cfg = nullptr) {
+                            size_t ws_bytes, cudaStream_t st, const dialsort_hist_config_t* cfg = nullptr,
+                            cudaEvent_t* marks = nullptr, bool* fused = nullptr) {
+  if (fused) *fused = false;
   dialsort_status_t s = check_keys(keys, key_bytes, n, U);
   if (s != DIALSORT_OK) return s;
   if (n > 0 && (out == nullptr || !aligned(out, key_bytes))) return DIALSORT_ERR_INVALID_ARG;
@@ -239,10 +241,12 @@ dialsort_status_t sort_impl(const void* keys, uint32_t key_bytes, uint64_t n, ui
     if ((s = plan_histogram(n, U, key_bytes, cfg ? cfg->skew : 0u, cfg, *dev, &plan)) != DIALSORT_OK) return s;
     const bool two_level = plan.tuned ? plan.regime == DIALSORT_REGIME_TWO_LEVEL
                                       : (plan.regime == DIALSORT_REGIME_GLOBAL_CRN || plan.regime == DIALSORT_REGIME_GLOBAL);
-    if (two_level && !keys_in_host && hier_fits(n, U, key_bytes, kp) && ib >= hier_layout(n, U).total)
+    if (two_level && !keys_in_host && hier_fits(n, U, key_bytes, kp) && ib >= hier_layout(n, U).total) {
+      if (fused) *fused = true;
       return from_cuda(launch_hier_sort(static_cast<const uint32_t*>(kp), n, U, H,
                                         static_cast<uint32_t*>(const_cast<void*>(op)), base + hb + rb,
-                                        hier_layout(n, U), *dev, dev->err, st));
+                                        hier_layout(n, U), *dev, dev->err, st, marks));
+    }
   }
   s = histogram_impl(keys, key_bytes, n, U, H, cfg, ib ? base + hb + rb : nullptr, ib, st);
   if (s != DIALSORT_OK) return s;
@@ -499,6 +503,34 @@ dialsort_status_t dialsort_sort_ex(const void* keys, uint32_t key_bytes, uint64_
 }
 
 uint32_t* dialsort_sort_histogram(void* ws) { return static_cast<uint32_t*>(ws); }
+
+dialsort_status_t dialsort_sort_stage_times(const void* keys, uint32_t key_bytes, uint64_t n, uint32_t U, void* out,
+                                            void* ws, size_t ws_bytes, void* stream, float* ms, uint32_t* stages) {
+  if (ms == nullptr || stages == nullptr) return DIALSORT_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  cudaEvent_t ev[5] = {};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+  dialsort_status_t s = DIALSORT_ERR_CUDA;
+  bool fused = false;
+  if (e == cudaSuccess && (e = cudaEventRecord(ev[0], st)) == cudaSuccess) {
+    s = sort_impl(keys, key_bytes, n, U, out, ws, ws_bytes, st, nullptr, ev + 1, &fused);
+    if (s == DIALSORT_OK && (e = cudaEventRecord(ev[4], st)) == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+    if (s == DIALSORT_OK && e != cudaSuccess) s = DIALSORT_ERR_CUDA;
+  }
+  if (s == DIALSORT_OK) {
+    if (fused) {  // pass 1 | split + schedule | counting fused with the projection | long runs
+      *stages = 4;
+      for (int i = 0; i < 4; ++i) cudaEventElapsedTime(ms + i, ev[i], ev[i + 1]);
+    } else {
+      *stages = 1;
+      cudaEventElapsedTime(ms, ev[0], ev[4]);
+    }
+  }
+  for (int i = 0; i < 5; ++i)
+    if (ev[i]) (void)cudaEventDestroy(ev[i]);
+  return s;
+}
 
 dialsort_status_t dialsort_stream_status(void* stream, int sync) {
   const DeviceInfo* dev = device_info();

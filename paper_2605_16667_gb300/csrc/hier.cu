@@ -102,7 +102,7 @@ __device__ __forceinline__ void load_tile(const uint32_t* __restrict__ keys, uin
 __device__ __forceinline__ uint32_t key_of(const uint4 (&kq)[4], int i) { return (&kq[i / 4].x)[i % 4]; }
 
 template <int BM, bool POW2>
-__global__ void __launch_bounds__(kP1Threads, 2) hier_partition_kernel(
+__global__ void __launch_bounds__(kP1Threads, 3) hier_partition_kernel(
     const uint32_t* __restrict__ keys, uint64_t n, uint32_t U, uint32_t B, uint64_t num_tiles, uint32_t S_t,
     uint16_t* __restrict__ low, uint32_t* __restrict__ seg, uint32_t* __restrict__ btot, uint32_t* err) {
   __shared__ P1Smem<BM> s;
@@ -116,13 +116,12 @@ __global__ void __launch_bounds__(kP1Threads, 2) hier_partition_kernel(
   const uint32_t pos_a = smem_addr(&s.pos[0][lane]);
   const uint32_t stage_a = smem_addr(s.stage);
   bool bad = false;
-  uint4 kc[4], kn[4];
+  uint4 kc[4];
   uint64_t t = blockIdx.x;
   if (t < num_tiles) load_tile(keys, n, t, warp, lane, kc);
   __syncthreads();
   while (t < num_tiles) {
     const uint64_t tn = t + gridDim.x;
-    if (tn < num_tiles) load_tile(keys, n, tn, warp, lane, kn);  // in flight while this tile is processed
     const uint32_t len = (uint32_t)min((uint64_t)kTile, n - t * kTile);
     // Are all 16 keys of this thread real and below U?  Do they share one bucket?
     const uint32_t k0 = kc[0].x;
@@ -236,8 +235,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) hier_partition_kernel(
     fence_proxy_async_smem();  // the stage writes, before the bulk store reads them
     __syncthreads();
     if (tid == 0 && padded_total) bulk_store(low + t * S_t, s.stage, padded_total * 2u);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) kc[j] = kn[j];
+    if (tn < num_tiles) load_tile(keys, n, tn, warp, lane, kc);  // (three CTAs per SM hide the load latency)
     t = tn;
   }
   if (tid == 0) bulk_wait_all();
@@ -935,7 +933,8 @@ cudaError_t launch_hier(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* 
 }
 
 cudaError_t launch_hier_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, uint32_t* out, void* ws,
-                             const HierLayout& T, const DeviceInfo& dev, uint32_t* err, cudaStream_t stream) {
+                             const HierLayout& T, const DeviceInfo& dev, uint32_t* err, cudaStream_t stream,
+                             cudaEvent_t* marks) {
   char* base = static_cast<char*>(ws);
   const uint16_t* low = reinterpret_cast<const uint16_t*>(base + T.off_low);
   const uint32_t* seg = reinterpret_cast<const uint32_t*>(base + T.off_seg);
@@ -948,6 +947,7 @@ cudaError_t launch_hier_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   uint32_t* pieces = reinterpret_cast<uint32_t*>(base + T.off_pieces);
   uint64_t* bbase = reinterpret_cast<uint64_t*>(base + T.off_bbase);
   cudaError_t e = launch_partition(keys, n, U, base, T, dev, err, stream);
+  if (e == cudaSuccess && marks) e = cudaEventRecord(marks[0], stream);
   if (e != cudaSuccess) return e;
   // count ranges: one per SM (measured faster than four: fewer pieces to flush), at least 2^17 keys each
   const uint32_t K = hier_count_ctas(n, (uint32_t)dev.sms);
@@ -962,6 +962,7 @@ cudaError_t launch_hier_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint3
   const uint32_t grid = (uint32_t)std::max(1, dev.sms * std::max(per_sm, 1));
   hier_sched_kernel<<<1, 1024, 0, stream>>>(start, K, btot, T.B, U, T.num_tiles, grid, sched, pieces, bbase, ctl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (marks && (e = cudaEventRecord(marks[1], stream)) != cudaSuccess) return e;
   const int aligned = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
   LongRun* longs = reinterpret_cast<LongRun*>(base + T.off_longs);
   uint32_t* pmap = reinterpret_cast<uint32_t*>(base + T.off_pmap);
@@ -969,6 +970,7 @@ cudaError_t launch_hier_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint3
                                                       pieces, bdone, bbase, desc, out, n, aligned, ctl, longs, pmap,
                                                       err);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (marks && (e = cudaEventRecord(marks[2], stream)) != cudaSuccess) return e;
   hier_long_kernel<<<dev.sms * 4, 256, 0, stream>>>(longs, pmap, ctl, out, aligned);
   return cudaGetLastError();
 }

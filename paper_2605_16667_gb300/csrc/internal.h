@@ -108,8 +108,11 @@ cudaError_t launch_hier(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* 
                         const DeviceInfo& dev, uint32_t* err, cudaStream_t stream, bool accumulate);
 // The whole sort of uint32 keys in the two-level form: pass 1, then counting fused with the projection
 // (Eq. (2)) into out (n_cap keys); H receives the histogram.
+// marks (or NULL): three events recorded after pass 1, after the split and schedule, and after the fused
+// kernel (the long-run painter follows).
 cudaError_t launch_hier_sort(const uint32_t* keys, uint64_t n, uint32_t U, uint32_t* H, uint32_t* out, void* ws,
-                             const HierLayout& T, const DeviceInfo& dev, uint32_t* err, cudaStream_t stream);
+                             const HierLayout& T, const DeviceInfo& dev, uint32_t* err, cudaStream_t stream,
+                             cudaEvent_t* marks = nullptr);
 
 // Self-tests of the bounded device waits (a wait that is made to run out).
 size_t offsets_selftest_bytes();

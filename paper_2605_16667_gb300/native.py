@@ -91,6 +91,7 @@ SIGNATURES = {
     "dialsort_sort": (STATUS, [P, U64, U32, P, P, SZ, P]),
     "dialsort_sort_u16": (STATUS, [P, U64, U32, P, P, SZ, P]),
     "dialsort_sort_ex": (STATUS, [P, U32, U64, U32, P, P, P, SZ, P]),
+    "dialsort_sort_stage_times": (STATUS, [P, U32, U64, U32, P, P, SZ, P, P, P]),
     "dialsort_sort_histogram": (P, [P]),
     "dialsort_batch_create": (STATUS, [P, U32, INT, P]),
     "dialsort_batch_workspace_size": (SZ, [P]),
