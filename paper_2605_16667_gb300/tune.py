@@ -11,8 +11,9 @@ line per shape and class (the format dialsort_tune_table_load reads):
 
 Skew classes and their inputs: 1 low conflict (uniform keys), 2 hot (Zipf
 s = 1.1 over [0, U)), 3 runs (the uniform keys sorted); class 0 (unknown)
-takes the candidate whose worst ratio to the best time over the three classes
-is smallest.  The cost model itself is always a candidate; a measured choice
+takes the candidate whose worst ratio to the cost model's time over the three
+classes is smallest, and only if it beats the cost model on every class (so an
+unprobed call is never slower than the cost model on any of them).  The cost model itself is always a candidate; a measured choice
 replaces it only when it is faster by more than `margin` (3 %), and where it
 is not the line says so with regime 0 (the cost model at that shape), so that
 the table never overrides the cost model on a noise win.
@@ -175,15 +176,15 @@ def tune_shape(lg_n: int, lg_u: int, width: int, sms: int, reps: int, margin: fl
         log(f"  n=2^{lg_n} U=2^{lg_u} w={width} skew={skew}: model {res['model']:.4f} ms, best {res[k]:.4f} ms "
             f"{configs[k] if k != 'model' else 'model'} -> {'table' if chosen else 'model'}")
         lines.append(table_line(lg_n, lg_u, width, skew, chosen, sms))
-    # unknown skew: the smallest worst-case ratio over the classes, among configs timed in every class
+    # unknown skew: a choice faster than the cost model on every class (by its worst ratio to the cost
+    # model's time), among configs timed in every class; else the cost model
     common = set(results[1]) & set(results[2]) & set(results[3])
-    best_c = {s: min(results[s].values()) for s in (1, 2, 3)}
 
     def worst(k):
-        return max(results[s][k] / best_c[s] for s in (1, 2, 3))
+        return max(results[s][k] / results[s]["model"] for s in (1, 2, 3))
 
     k = min(common, key=worst)
-    chosen = configs[k] if worst(k) * (1.0 + margin) < worst("model") else None
+    chosen = configs[k] if worst(k) * (1.0 + margin) < 1.0 else None
     lines.append(table_line(lg_n, lg_u, width, 0, chosen, sms))
     return lines
 
