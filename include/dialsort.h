@@ -81,7 +81,7 @@ typedef enum {
 /* Skew classes of a key sequence (dialsort_probe_skew; the autotuner's table
  * is keyed by them).  How often equal keys meet decides what the CRN's merge
  * saves and how contended the counters get (Sec. "Conflict Resolution
- * Network", the remark on skewed inputs). */
+ * Network (CRN)", subsection "Performance consequence under skewed input"). */
 typedef enum {
   DIALSORT_SKEW_UNKNOWN = 0,
   DIALSORT_SKEW_LOW = 1,    /* few equal keys meet: near uniform over a large universe */

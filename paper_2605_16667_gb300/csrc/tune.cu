@@ -2,8 +2,8 @@
 // measured launch choices per (n, U, key width, skew class).
 //
 // Skew probe.  How much the CRN pays, and how contended the counters get,
-// depends on how often equal keys meet (the paper's remark on the CRN under
-// skew, Sec. "Conflict Resolution Network").  One CTA samples 128 windows of
+// depends on how often equal keys meet (Sec. "Conflict Resolution Network
+// (CRN)", subsection "Performance consequence under skewed input").  One CTA samples 128 windows of
 // 32 consecutive keys spread over the input and measures, with equality tests
 // only:
 //   adjacent  how many neighbours in a window are equal (sorted input and
