@@ -3,22 +3,27 @@
 // (Eq. (1) with U = 256) and place every key at its digit's cursor (Eq. (2)'s
 // projection, carrying the key instead of the digit).  LSD needs each pass to
 // be stable, so placement keeps input order among equal digits.  Signed keys
-// sort by flipping the sign bit of the top digit.  Keys are only ever split
-// into digits; no two keys are compared by magnitude.
+// sort as unsigned words with the sign bit flipped (two's complement order).
+// Keys are only ever split into digits; no two keys are compared by magnitude.
 //
-// GPU layout of one pass (one kernel, tiles of 16384 keys taken in ticket
-// order):
-//   * warp w of the CTA holds keys [512 w, 512 w + 512) of the tile, lane l
-//     key 32 i + l in step i, so the order (step, lane) is input order;
-//   * in each step the warp finds the lanes with the same digit from 8
-//     ballots (one per digit bit) and ranks them by lane: a stable rank with
-//     no atomics; per-warp digit counters carry the rank across steps;
+// GPU layout of one pass (one kernel per pass with the digit fixed at compile
+// time; 512-thread CTAs, two per SM; tiles of 8192 keys taken in ticket order):
+//   * warp w of the CTA holds keys [512 w, 512 w + 512) of the tile in
+//     registers, lane l key 32 i + l in step i, so the order (step, lane) is
+//     input order;
+//   * in each step every lane ORs its bit into a per-warp shared-memory table
+//     entry of its digit and reads the entry back: the lanes holding the same
+//     digit, found by equality alone (the digit indexes the table); the
+//     rank is the number of lower lanes among them plus a per-warp digit
+//     counter that carries it across steps (a warp whose 32 keys share the
+//     digit skips the table);
 //   * a scan over (digit, warp) gives each key its slot in the tile's stable
 //     digit order; keys are staged there in shared memory;
-//   * the tile's per-digit counts are chained to the earlier tiles' by a
-//     decoupled look-back (one thread per digit), giving every digit run of
-//     the tile its global start = digit base + keys of that digit in earlier
-//     tiles;
+//   * the tile's per-digit counts are published as soon as they are known and
+//     chained to the earlier tiles' by a decoupled look-back (one thread per
+//     digit, four earlier tiles read per round with relaxed loads), giving
+//     every digit run of the tile its global start = digit base + keys of
+//     that digit in earlier tiles;
 //   * the staged keys are written out, runs of one digit to consecutive
 //     addresses.
 // The global digit bases come from a histogram of the pass's digit over all
@@ -32,10 +37,11 @@
 namespace dialsort {
 namespace {
 
-constexpr uint32_t kRxThreads = 1024;
+constexpr uint32_t kRxThreads = 512;                    // two CTAs per SM
 constexpr uint32_t kRxWarps = kRxThreads / 32;
 constexpr uint32_t kRxSteps = 16;                       // keys per thread
-constexpr uint32_t kRxTile = kRxThreads * kRxSteps;     // 16384 keys per tile
+constexpr uint32_t kRxTile = kRxThreads * kRxSteps;     // 8192 keys per tile
+constexpr uint32_t kRxWindow = 4;                       // earlier tiles read per look-back round
 constexpr uint32_t kRxDigits = 256;
 constexpr uint32_t kRxPasses = 4;
 
@@ -47,9 +53,30 @@ __device__ __forceinline__ uint64_t rx_desc(uint32_t state, uint32_t value) {
   return ((uint64_t)state << 32) | value;
 }
 
-__device__ __forceinline__ uint32_t rx_digit(uint32_t x, uint32_t pass, bool is_signed) {
-  const uint32_t d = (x >> (8u * pass)) & 0xffu;
-  return (is_signed && pass == kRxPasses - 1) ? (d ^ 0x80u) : d;  // two's complement order
+// A descriptor word carries its state and its count together, and the look-back reads nothing else that
+// the tile it describes wrote, so relaxed accesses suffice -- and, unlike acquire loads, a window of them
+// can be in flight at once.
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Signed keys are sorted as unsigned words with the sign bit flipped (two's complement order): the
+// first pass flips it on the way in, the last flips it back on the way out, so every digit is a byte.
+template <uint32_t PASS>
+__device__ __forceinline__ uint32_t rx_byte(uint32_t x) {
+  return (x >> (8u * PASS)) & 0xffu;
+}
+
+__device__ __forceinline__ void red_or_shared(uint32_t* p, uint32_t v) {
+  asm volatile("red.shared.or.b32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared(uint32_t* p, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
 
 // Add 1 to h[d] for every lane; when all 32 lanes hold the same digit (keys
@@ -57,9 +84,9 @@ __device__ __forceinline__ uint32_t rx_digit(uint32_t x, uint32_t pass, bool is_
 __device__ __forceinline__ void rx_count(uint32_t* h, uint32_t d, uint32_t lane) {
   const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
   if (__all_sync(0xffffffffu, d == d0)) {
-    if (lane == 0) atomicAdd(h + d, 32u);
+    if (lane == 0) red_add_shared(h + d, 32u);
   } else {
-    atomicAdd(h + d, 1u);
+    red_add_shared(h + d, 1u);
   }
 }
 
@@ -80,25 +107,24 @@ __global__ void __launch_bounds__(kRxThreads) rx_count_kernel(const uint32_t* __
   const uint64_t stride = (uint64_t)gridDim.x * kRxThreads;
   const uint64_t vend = (nvec + 31u) & ~31ull;  // whole warps iterate together
   for (uint64_t v = (uint64_t)blockIdx.x * kRxThreads + tid; v < vend; v += stride) {
-    if (v < nvec) {
-      const uint4 q = ld_stream_v4(k4 + v);
-      if (__activemask() == 0xffffffffu) {
-        rx_count(mine, q.x & 0xffu, lane);
-        rx_count(mine, q.y & 0xffu, lane);
-        rx_count(mine, q.z & 0xffu, lane);
-        rx_count(mine, q.w & 0xffu, lane);
-      } else {
-        atomicAdd(mine + (q.x & 0xffu), 1u);
-        atomicAdd(mine + (q.y & 0xffu), 1u);
-        atomicAdd(mine + (q.z & 0xffu), 1u);
-        atomicAdd(mine + (q.w & 0xffu), 1u);
-      }
+    const bool ok = v < nvec;  // (the loop bound is warp-uniform: vend and the stride are multiples of 32)
+    const uint4 q = ok ? ld_stream_v4(k4 + v) : make_uint4(0u, 0u, 0u, 0u);
+    if (__all_sync(0xffffffffu, ok)) {
+      rx_count(mine, q.x & 0xffu, lane);
+      rx_count(mine, q.y & 0xffu, lane);
+      rx_count(mine, q.z & 0xffu, lane);
+      rx_count(mine, q.w & 0xffu, lane);
+    } else if (ok) {
+      red_add_shared(mine + (q.x & 0xffu), 1u);
+      red_add_shared(mine + (q.y & 0xffu), 1u);
+      red_add_shared(mine + (q.z & 0xffu), 1u);
+      red_add_shared(mine + (q.w & 0xffu), 1u);
     }
   }
   if (blockIdx.x == 0) {
     const uint64_t tail0 = head + nvec * 4;
     for (uint64_t i = tid; i < head + (n - tail0); i += kRxThreads)
-      atomicAdd(mine + (keys[i < head ? i : tail0 + (i - head)] & 0xffu), 1u);
+      red_add_shared(mine + (keys[i < head ? i : tail0 + (i - head)] & 0xffu), 1u);
   }
   __syncthreads();
   for (uint32_t d = tid; d < kRxDigits; d += kRxThreads) {
@@ -108,9 +134,9 @@ __global__ void __launch_bounds__(kRxThreads) rx_count_kernel(const uint32_t* __
 }
 
 struct RxSmem {
-  uint32_t in[kRxTile];                  // the tile's keys in input order (frees registers across the scan)
   uint32_t stage[kRxTile];               // the tile's keys in stable digit order
-  uint16_t wcnt[kRxWarps][kRxDigits];    // per-warp digit counters, then per-warp digit bases
+  uint32_t peer[kRxWarps][2][kRxDigits]; // per warp, two alternating tables: lanes (bit masks) holding each digit
+  uint16_t wcnt[kRxWarps][kRxDigits];    // per-warp digit counters, then per-warp digit slots in the tile
   uint32_t gpos[kRxDigits];              // global position of the tile's first key of each digit
   uint32_t gbase[kRxDigits];             // global start of each digit
   uint32_t next[kRxDigits];              // histogram of the next pass's digit (this CTA)
@@ -147,74 +173,103 @@ __device__ __forceinline__ uint32_t scan256(uint32_t v, uint32_t* red, uint32_t*
   return r;
 }
 
-template <bool kSigned>
-__global__ void __launch_bounds__(kRxThreads, 1) rx_pass_kernel(const uint32_t* __restrict__ src,
+// Load this thread's keys of a tile (step i, lane l -> key 32 i + l of the warp's 512; FLIP is xored in)
+// and rank each among the warp's keys of the same digit in (step, lane) order, i.e. input order.
+// The lanes holding a digit are found with equality only: each lane sets its bit in the step's table
+// entry of its digit, then reads the entry back (one table per step parity; each step clears the
+// previous step's entries).  A warp whose keys all share the digit skips the table.  Ranks go to rk as
+// 16-bit pairs; wcnt[warp][d] ends as the warp's count of digit d.  FULL: the whole tile lies below n.
+template <uint32_t PASS, bool FULL>
+__device__ __forceinline__ void rx_load_rank(const uint32_t* __restrict__ src, uint32_t lim, uint32_t flip,
+                                             uint32_t (&kv)[kRxSteps], uint32_t (&rk)[kRxSteps / 2], RxSmem& S) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t off = warp * (kRxSteps * 32u) + lane;  // this lane's key 0 in the tile
+  const uint32_t* q = src + off;
+#pragma unroll
+  for (uint32_t i = 0; i < kRxSteps; ++i) kv[i] = (FULL || off + 32u * i < lim) ? q[32u * i] ^ flip : 0u;
+  const uint32_t lt = lanemask_lt(), bit = 1u << lane;
+  uint16_t* wc = S.wcnt[warp];
+  uint32_t* tab = S.peer[warp][0];
+  uint32_t dprev = 0;
+  bool prev_used = false;
+#pragma unroll
+  for (uint32_t i = 0; i < kRxSteps; ++i) {
+    const bool valid = FULL || off + 32u * i < lim;
+    const uint32_t d = rx_byte<PASS>(kv[i]);
+    const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);  // every lane takes part, keys or not
+    const bool uni = __all_sync(0xffffffffu, valid && d == d0);
+    uint32_t* cur = tab + (i & 1u) * kRxDigits;
+    if (!uni && valid) red_or_shared(cur + d, bit);
+    __syncwarp();  // every lane's bit is in; the previous step's leader update of wc is visible
+    const uint32_t peers = uni ? 0xffffffffu : (valid ? cur[d] : 0u);
+    if (prev_used) tab[((i + 1u) & 1u) * kRxDigits + dprev] = 0u;  // the previous step's table was read
+    prev_used = !uni;
+    dprev = d;
+    const uint32_t before = wc[d];
+    const uint32_t r = before + __popc(peers & lt);
+    __syncwarp();  // every lane has read wc and the previous table before they change
+    if (valid && (peers & lt) == 0) wc[d] = (uint16_t)(before + __popc(peers));
+    if (i % 2 == 0)
+      rk[i / 2] = r;
+    else
+      rk[i / 2] |= r << 16;
+  }
+  if (prev_used) tab[((kRxSteps - 1u) & 1u) * kRxDigits + dprev] = 0u;
+  __syncwarp();
+}
+
+// One LSD pass on byte PASS.  Tiles of kRxTile keys are taken in ticket order; each is ranked stably in
+// registers, its per-digit count published at once (so that later tiles can add it without waiting),
+// its per-digit prefix over earlier tiles found by a decoupled look-back, and its keys staged in stable
+// digit order and written out, runs of one digit to consecutive addresses.  The next pass's digit is
+// counted on the way out.  kSigned: the sign bit is flipped in pass 0 and flipped back in pass 3.
+template <bool kSigned, uint32_t PASS>
+__global__ void __launch_bounds__(kRxThreads, 2) rx_pass_kernel(const uint32_t* __restrict__ src,
                                                                 uint32_t* __restrict__ dst, uint64_t n,
-                                                                uint32_t pass, uint64_t num_tiles,
-                                                                uint32_t* __restrict__ ghist,
+                                                                uint64_t num_tiles, uint32_t* __restrict__ ghist,
                                                                 uint64_t* __restrict__ desc,
                                                                 uint32_t* __restrict__ tickets, uint32_t* err) {
   extern __shared__ __align__(16) unsigned char rx_raw[];
   RxSmem& S = *reinterpret_cast<RxSmem*>(rx_raw);
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  const bool count_next = pass + 1 < kRxPasses;
+  constexpr bool count_next = PASS + 1 < kRxPasses;
+  constexpr uint32_t agg_state = 2u * PASS + 1u, inc_state = 2u * PASS + 2u;
+  const uint32_t flip_in = (kSigned && PASS == 0) ? 0x80000000u : 0u;
+  const uint32_t flip_out = (kSigned && PASS == kRxPasses - 1) ? 0x80000000u : 0u;
 
   // global digit starts of this pass: exclusive scan of its histogram
   {
     uint32_t total;
-    const uint32_t c = tid < kRxDigits ? ghist[pass * kRxDigits + tid] : 0u;
+    const uint32_t c = tid < kRxDigits ? ghist[PASS * kRxDigits + tid] : 0u;
     const uint32_t ex = scan256(c, S.red, &total);
     if (tid < kRxDigits) {
       S.gbase[tid] = ex;
       S.next[tid] = 0;
     }
   }
+  for (uint32_t i = tid; i < kRxWarps * 2 * kRxDigits; i += kRxThreads) (&S.peer[0][0][0])[i] = 0;
   bool timed_out = false;
 
   for (;;) {
-    if (tid == 0) S.tile = atomicAdd(tickets + pass, 1u);
+    if (tid == 0) S.tile = atomicAdd(tickets + PASS, 1u);
     for (uint32_t i = tid; i < kRxWarps * kRxDigits / 2; i += kRxThreads)
       reinterpret_cast<uint32_t*>(&S.wcnt[0][0])[i] = 0;
     __syncthreads();
     const uint64_t t = S.tile;
     if (t >= num_tiles) break;
-    const uint64_t base = t * kRxTile + (uint64_t)warp * (kRxSteps * 32u);
-
-    // load (striped: step i, lane l -> key 32 i + l of the warp's 512) and rank stably
-    uint32_t kv[kRxSteps];
-    uint32_t* in = S.in + warp * (kRxSteps * 32u) + lane;
-#pragma unroll
-    for (uint32_t i = 0; i < kRxSteps; ++i) {
-      const uint64_t p = base + 32u * i + lane;
-      kv[i] = p < n ? src[p] : 0u;
-      in[32u * i] = kv[i];
-    }
-    uint32_t rk[kRxSteps / 2];
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (uint32_t i = 0; i < kRxSteps; ++i) {
-      const bool valid = base + 32u * i + lane < n;
-      const uint32_t d = rx_digit(kv[i], pass, kSigned);
-      uint32_t peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-      for (uint32_t b = 0; b < 8; ++b) {
-        const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-        peers &= ((d >> b) & 1u) ? m : ~m;
-      }
-      const uint32_t before = S.wcnt[warp][d];
-      const uint32_t r = before + __popc(peers & lt);
-      __syncwarp();
-      if (valid && (peers & lt) == 0) S.wcnt[warp][d] = (uint16_t)(before + __popc(peers));
-      __syncwarp();
-      if (i % 2 == 0)
-        rk[i / 2] = r;
-      else
-        rk[i / 2] |= r << 16;
-    }
+    const uint64_t tbase = t * kRxTile;
+    const bool full = tbase + kRxTile <= n;
+    const uint32_t lim = full ? kRxTile : (uint32_t)(n - tbase);
+    uint32_t kv[kRxSteps], rk[kRxSteps / 2];
+    if (full)
+      rx_load_rank<PASS, true>(src + tbase, lim, flip_in, kv, rk, S);
+    else
+      rx_load_rank<PASS, false>(src + tbase, lim, flip_in, kv, rk, S);
     __syncthreads();
 
-    // per digit: warp bases (in place) and the tile's count; then digit starts in the tile
+    // per digit: the warps' counts become their slots within the digit; publish the tile's count
     uint32_t cnt = 0;
+    uint64_t* my = desc + t * kRxDigits + tid;
     if (tid < kRxDigits) {
 #pragma unroll
       for (uint32_t w = 0; w < kRxWarps; ++w) {
@@ -222,87 +277,105 @@ __global__ void __launch_bounds__(kRxThreads, 1) rx_pass_kernel(const uint32_t* 
         S.wcnt[w][tid] = (uint16_t)cnt;
         cnt += c;
       }
+      st_relaxed_u64(my, rx_desc(t == 0 ? inc_state : agg_state, cnt));
     }
     uint32_t tile_valid;
     const uint32_t start = scan256(cnt, S.red, &tile_valid);
     if (tid < kRxDigits) {
 #pragma unroll
       for (uint32_t w = 0; w < kRxWarps; ++w) S.wcnt[w][tid] = (uint16_t)(S.wcnt[w][tid] + start);
-      // publish this tile's count, then look back over earlier tiles for the digit's prefix
-      uint64_t* my = desc + t * kRxDigits + tid;
-      const uint32_t agg = 2u * pass + 1u, inc = 2u * pass + 2u;
-      if (t == 0) {
-        st_release_u64(my, rx_desc(inc, cnt));
-        S.gpos[tid] = S.gbase[tid] - start;
-      } else {
-        st_release_u64(my, rx_desc(agg, cnt));
-        uint32_t prefix = 0;
-        uint64_t tt = t - 1;
+      // look back over earlier tiles for the digit's prefix, kRxWindow tiles per round: the counts of a
+      // run of published tiles add up until one that carries its inclusive prefix
+      uint32_t prefix = 0;
+      if (t > 0) {
+        uint64_t tt = t - 1;  // the next earlier tile not yet added
         uint32_t spins = 0;
         for (;;) {
-          const uint64_t v = ld_acquire_u64(desc + tt * kRxDigits + tid);
-          const uint32_t state = (uint32_t)(v >> 32);
-          if (state == inc) {
-            prefix += (uint32_t)v;
-            break;
+          uint64_t v[kRxWindow];
+#pragma unroll
+          for (uint32_t j = 0; j < kRxWindow; ++j) v[j] = j <= tt ? ld_relaxed_u64(desc + (tt - j) * kRxDigits + tid) : 0ull;
+          uint32_t used = 0;
+          bool done = false;
+#pragma unroll
+          for (uint32_t j = 0; j < kRxWindow; ++j) {
+            if (done || used != j || j > tt) continue;
+            const uint32_t state = (uint32_t)(v[j] >> 32);
+            if (state == inc_state) {
+              prefix += (uint32_t)v[j];
+              done = true;
+            } else if (state == agg_state) {
+              prefix += (uint32_t)v[j];
+              used = j + 1;
+            }
           }
-          if (state == agg) {
-            prefix += (uint32_t)v;
-            if (tt == 0) break;  // (tile 0 publishes inclusive only; kept for safety)
-            --tt;
+          if (done) break;
+          if (used > 0) {  // tile 0 always publishes its inclusive count, so tt stays >= 0 here
+            tt -= used;
             continue;
           }
-          if (++spins >= kSpinLimit) {  // predecessor never published: give up, report
+          if (++spins >= kSpinLimit) {  // tile tt never published: give up, report
             timed_out = true;
             break;
           }
           __nanosleep(64);
         }
-        st_release_u64(my, rx_desc(inc, prefix + cnt));
-        S.gpos[tid] = S.gbase[tid] + prefix - start;
+        st_relaxed_u64(my, rx_desc(inc_state, prefix + cnt));
       }
+      S.gpos[tid] = S.gbase[tid] + prefix - start;
     }
     __syncthreads();
 
     // stage every key at its slot in the tile's stable digit order
+    {
+      const uint32_t off = warp * (kRxSteps * 32u) + lane;
+      const uint16_t* wc = S.wcnt[warp];
 #pragma unroll
-    for (uint32_t i = 0; i < kRxSteps; ++i) {
-      if (base + 32u * i + lane < n) {
-        const uint32_t x = in[32u * i];
-        const uint32_t d = rx_digit(x, pass, kSigned);
-        const uint32_t r = (rk[i / 2] >> (16 * (i & 1))) & 0xffffu;
-        S.stage[S.wcnt[warp][d] + r] = x;
+      for (uint32_t i = 0; i < kRxSteps; ++i) {
+        if (full || off + 32u * i < lim) {
+          const uint32_t r = (rk[i / 2] >> (16 * (i & 1))) & 0xffffu;
+          S.stage[wc[rx_byte<PASS>(kv[i])] + r] = kv[i];
+        }
       }
     }
     __syncthreads();
-    // write out: consecutive slots of one digit go to consecutive addresses
     // write out: consecutive slots of one digit go to consecutive addresses; the next pass's digit is
     // counted on the way (gpos[d] holds the digit's global start minus its start in the tile)
+#pragma unroll 4
     for (uint32_t j0 = warp * 32u; j0 < tile_valid; j0 += kRxThreads) {  // warp-uniform bound
       const uint32_t j = j0 + lane;
       const bool valid = j < tile_valid;
       const uint32_t x = valid ? S.stage[j] : 0u;
       if (valid) {
-        const uint32_t pos = S.gpos[rx_digit(x, pass, kSigned)] + j;  // mod 2^32: exact, since n < 2^32
-        if (pos < n) dst[pos] = x;  // always true unless a look-back timed out
+        const uint32_t pos = S.gpos[rx_byte<PASS>(x)] + j;  // mod 2^32: exact, since n < 2^32
+        if (pos < n) dst[pos] = x ^ flip_out;  // always true unless a look-back timed out
       }
-      if (count_next) {  // one add of 32 when the warp's keys share the next digit (small keys, a constant byte)
-        const uint32_t dn = rx_digit(x, pass + 1, kSigned);
-        const uint32_t d0 = __shfl_sync(0xffffffffu, dn, 0);
+      if (count_next) {
+        const uint32_t dn = rx_byte<(PASS + 1) % kRxPasses>(x);
+        const uint32_t d0 = __shfl_sync(0xffffffffu, dn, 0);  // every lane takes part, keys or not
         if (__all_sync(0xffffffffu, valid && dn == d0)) {
-          if (lane == 0) atomicAdd(&S.next[dn], 32u);
+          if (lane == 0) red_add_shared(&S.next[dn], 32u);
         } else if (valid) {
-          atomicAdd(&S.next[dn], 1u);
+          red_add_shared(&S.next[dn], 1u);
         }
       }
     }
-    __syncthreads();
+    // (the next tile's first barrier orders these reads of stage and gpos before their next writes)
   }
   if (timed_out) raise_error(err, ERRBIT_TIMEOUT);
   if (count_next) {
     __syncthreads();
     for (uint32_t d = tid; d < kRxDigits; d += kRxThreads)
-      if (S.next[d]) red_add_global(ghist + (pass + 1) * kRxDigits + d, S.next[d]);
+      if (S.next[d]) red_add_global(ghist + (PASS + 1) * kRxDigits + d, S.next[d]);
+  }
+}
+
+template <bool kSigned>
+const void* rx_pass_fn(uint32_t pass) {
+  switch (pass) {
+    case 0: return reinterpret_cast<const void*>(&rx_pass_kernel<kSigned, 0>);
+    case 1: return reinterpret_cast<const void*>(&rx_pass_kernel<kSigned, 1>);
+    case 2: return reinterpret_cast<const void*>(&rx_pass_kernel<kSigned, 2>);
+    default: return reinterpret_cast<const void*>(&rx_pass_kernel<kSigned, 3>);
   }
 }
 
@@ -360,27 +433,22 @@ dialsort_status_t radix_impl(const uint32_t* keys, uint64_t n, uint32_t* out, vo
   rx_count_kernel<<<cgrid, kRxThreads, 0, st>>>(keys, n, ghist);
   if (cudaGetLastError() != cudaSuccess) return DIALSORT_ERR_CUDA;
 
-  const void* fn = is_signed ? reinterpret_cast<const void*>(&rx_pass_kernel<true>)
-                             : reinterpret_cast<const void*>(&rx_pass_kernel<false>);
   const size_t smem = sizeof(RxSmem);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return DIALSORT_ERR_CUDA;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRxThreads, smem) != cudaSuccess)
-    return DIALSORT_ERR_CUDA;
   // tiles go out in ticket order, so a tile waits only on tiles whose CTAs are already running
-  const unsigned grid = (unsigned)std::min<uint64_t>(R.num_tiles, (uint64_t)dev->sms * std::max(per_sm, 1));
   // ping-pong: keys -> tmp -> out -> tmp -> out (out may be keys: pass 0 and the count read keys first)
   const uint32_t* srcs[kRxPasses] = {keys, tmp, out, tmp};
   uint32_t* dsts[kRxPasses] = {tmp, out, tmp, out};
   uint64_t num_tiles = R.num_tiles;
   for (uint32_t p = 0; p < kRxPasses; ++p) {
+    const void* fn = is_signed ? rx_pass_fn<true>(p) : rx_pass_fn<false>(p);
+    if (kernel_config(fn, kRxThreads, smem, false, &per_sm) != cudaSuccess) return DIALSORT_ERR_CUDA;
+    const unsigned grid = (unsigned)std::min<uint64_t>(R.num_tiles, (uint64_t)dev->sms * std::max(per_sm, 1));
     const uint32_t* sp = srcs[p];
     uint32_t* dp = dsts[p];
-    uint32_t pass = p;
     uint64_t nn = n;
     uint32_t* err = dev->err;
-    void* args[] = {&sp, &dp, &nn, &pass, &num_tiles, &ghist, &desc, &tickets, &err};
+    void* args[] = {&sp, &dp, &nn, &num_tiles, &ghist, &desc, &tickets, &err};
     if (cudaLaunchKernel(fn, dim3(grid), dim3(kRxThreads), args, smem, st) != cudaSuccess) return DIALSORT_ERR_CUDA;
   }
   return DIALSORT_OK;
@@ -401,13 +469,13 @@ cudaError_t launch_radix_selftest(void* ws, uint32_t* err, cudaStream_t stream) 
   if (e == cudaSuccess) e = cudaMemsetAsync(base + R.off_tickets, 1, 1, stream);  // pass 0's ticket = 1
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(RxSmem);
-  e = cudaFuncSetAttribute(rx_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = kernel_config(reinterpret_cast<const void*>(&rx_pass_kernel<false, 0>), kRxThreads, smem, false, nullptr);
   if (e != cudaSuccess) return e;
   uint32_t* tmp = reinterpret_cast<uint32_t*>(base + R.off_tmp);
-  rx_pass_kernel<false><<<1, kRxThreads, smem, stream>>>(tmp, tmp, n, 0u, R.num_tiles,
-                                                          reinterpret_cast<uint32_t*>(base + R.off_ghist),
-                                                          reinterpret_cast<uint64_t*>(base + R.off_desc),
-                                                          reinterpret_cast<uint32_t*>(base + R.off_tickets), err);
+  rx_pass_kernel<false, 0><<<1, kRxThreads, smem, stream>>>(tmp, tmp, n, R.num_tiles,
+                                                             reinterpret_cast<uint32_t*>(base + R.off_ghist),
+                                                             reinterpret_cast<uint64_t*>(base + R.off_desc),
+                                                             reinterpret_cast<uint32_t*>(base + R.off_tickets), err);
   return cudaGetLastError();
 }
 

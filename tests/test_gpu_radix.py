@@ -31,11 +31,13 @@ def cases():
     yield "empty", np.zeros(0, dtype=np.uint32)
     yield "one", np.array([0xDEADBEEF], dtype=np.uint32)
     yield "8191", full_range(8191, 9400)
+    yield "8192", full_range(8192, 9423)  # one whole tile of 8192 keys
     yield "8193", full_range(8193, 9402)
-    yield "tile-1", full_range(16383, 9420)  # tiles of 16384 keys
+    yield "tile-1", full_range(16383, 9420)
     yield "tile", full_range(16384, 9401)
     yield "tile+1", full_range(16385, 9421)
     yield "3tiles+5", full_range(3 * 16384 + 5, 9422)
+    yield "303tiles+77", full_range(303 * 8192 + 77, 9424)  # more tiles than two CTAs per SM hold at once
     yield "ragged", full_range(1_000_003, 9403)
     yield "zipf-small", gen.keys(2_000_001, 1 << 20, "zipf", stream=9404)  # top two digits all zero
     yield "all-equal", np.full(300_001, 0x80000000, dtype=np.uint32)
