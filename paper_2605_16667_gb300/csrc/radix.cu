@@ -284,6 +284,9 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_pass_kernel(const uint32_t* 
     if (tid < kRxDigits) {
 #pragma unroll
       for (uint32_t w = 0; w < kRxWarps; ++w) S.wcnt[w][tid] = (uint16_t)(S.wcnt[w][tid] + start);
+    }
+    __syncthreads();  // every key's slot is known: warps past the first 256 threads stage during the look-back
+    if (tid < kRxDigits) {
       // look back over earlier tiles for the digit's prefix, kRxWindow tiles per round: the counts of a
       // run of published tiles add up until one that carries its inclusive prefix
       uint32_t prefix = 0;
@@ -323,7 +326,6 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_pass_kernel(const uint32_t* 
       }
       S.gpos[tid] = S.gbase[tid] + prefix - start;
     }
-    __syncthreads();
 
     // stage every key at its slot in the tile's stable digit order
     {
